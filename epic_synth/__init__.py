@@ -167,8 +167,8 @@ def config(idx: int) -> EpicConfig:
 
 def pack_nibbles(re: np.ndarray, im: np.ndarray) -> np.ndarray:
     """Pack integer parts in [-8, 7] as one byte: real high nibble, imaginary low."""
-    re = np.asarray(re, dtype=np.int64)
-    im = np.asarray(im, dtype=np.int64)
+    re = np.asarray(re).astype(np.int16)
+    im = np.asarray(im).astype(np.int16)
     if re.size and (re.min() < -8 or re.max() > 7 or im.min() < -8 or im.max() > 7):
         raise ValueError("value outside the 4-bit two's-complement range")
     return (((re & 0xF) << 4) | (im & 0xF)).astype(np.uint8)
@@ -183,24 +183,32 @@ def source_phases(cfg: EpicConfig) -> np.ndarray:
 
 def make_voltages(cfg: EpicConfig, t0: int = 0, n_time: Optional[int] = None,
                   out: Optional[np.ndarray] = None) -> np.ndarray:
-    """uint8[T][C][A][P] packed 4+4-bit voltages for time samples [t0, t0+T)."""
+    """uint8[T][C][A][P] packed 4+4-bit voltages for time samples [t0, t0+T).
+
+    Noise and source amplitudes are drawn in float32 from the stream of each
+    time sample; the source term is a batched (A x S) @ (S x P) product per
+    channel.
+    """
     T = cfg.n_time - t0 if n_time is None else int(n_time)
     C, A, P = cfg.n_chan, cfg.n_ant, cfg.n_pol
     S = cfg.src_lm.shape[0]
     if out is None:
         out = np.empty((T, C, A, P), dtype=np.uint8)
-    ph = source_phases(cfg) if S else None                      # [C][A][S]
+    ph = source_phases(cfg).astype(np.complex64) if S else None       # [C][A][S]
+    amp = (cfg.src_amp / math.sqrt(2.0)).astype(np.float32)
     for i in range(T):
         rng = np.random.default_rng([cfg.seed, t0 + i])
-        noise = rng.normal(0.0, cfg.noise_sigma, size=(C, A, P, 2))
-        e = noise[..., 0] + 1j * noise[..., 1]
+        noise = rng.standard_normal(size=(C, A, P, 2), dtype=np.float32)
+        noise *= np.float32(cfg.noise_sigma)
+        re = noise[..., 0]
+        im = noise[..., 1]
         if S:
-            g = rng.normal(0.0, 1.0, size=(C, P, S, 2))
-            a = (g[..., 0] + 1j * g[..., 1]) * (cfg.src_amp / math.sqrt(2.0))  # [C][P][S]
-            e = e + np.einsum("cas,cps->cap", ph, a)
-        re = np.clip(np.rint(e.real), -7, 7)
-        im = np.clip(np.rint(e.imag), -7, 7)
-        out[i] = pack_nibbles(re, im)
+            g = rng.standard_normal(size=(C, S, P, 2), dtype=np.float32)
+            a = (g[..., 0] + 1j * g[..., 1]) * amp[None, :, None]          # [C][S][P]
+            src = np.matmul(ph, a.astype(np.complex64))                    # [C][A][P]
+            re = re + src.real
+            im = im + src.imag
+        out[i] = pack_nibbles(np.clip(np.rint(re), -7, 7), np.clip(np.rint(im), -7, 7))
     return out
 
 

@@ -1,0 +1,174 @@
+/*
+ * epic.h -- C ABI of the GB300 EPIC imaging library (libepic.so).
+ *
+ * EPIC (E-field Parallel Imaging "Correlator", paper Sec. 2) turns channelised,
+ * calibrated element voltages into all-sky polarised intensity images without
+ * forming pairwise correlations:
+ *   Eq. 1  grid the voltages of every element onto a regular aperture grid with a
+ *          gridding convolution function (GCF), then take a 2-D spatial Fourier
+ *          transform (the paper implements it as an FFT);
+ *   Eq. 2  form the pixelwise outer product of the polarisations and average it
+ *          over the integration time.
+ * One call of epic_image runs, on the GPU, for every time sample, channel and
+ * polarisation of a voltage block: 4+4-bit unpack -> gridding -> 2-D transform
+ * -> XX/YY/XY products -> accumulation (Sec. 2, Eq. 1-2; 4-bit input and the
+ * power-of-two grid finer than lambda/2 follow the workload of Sec. 4).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an epic_status; nothing throws across the ABI.
+ *   - Voltages: uint8 [T][n_chan][n_ant][n_pol], one byte per complex sample,
+ *     real part in the high nibble, imaginary in the low nibble, 4-bit two's
+ *     complement (values -8..7).
+ *   - Images: float32 [n_chan][n_prod][N][N], n_prod = 1 (XX) for one pol and
+ *     4 (XX, YY, Re XY, Im XY; XY = E_X conj(E_Y), YX = conj(XY) not stored) for
+ *     two.  Row index = m (y), column = l (x); index i holds direction cosine
+ *     (i - N/2) * lambda_c / (N * Delta_c) (zero direction at N/2, "fftshifted").
+ *   - The transform has the + sign of Eq. 1, no 1/N factor, and unit cell area
+ *     (delta^2 r_j = 1).  The images are SUMS over the block's time samples; divide
+ *     by T for the average of Eq. 2.
+ *   - Grid geometry: cell spacing Delta_c (default lambda_c/2), origin at the array
+ *     centroid placed at cell (N/2, N/2).  Odd K: anchor = nearest cell (ties up),
+ *     taps anchor +- (K-1)/2; even K: taps floor(u)-K/2+1 .. floor(u)+K/2.  No tap
+ *     may leave the grid (EPIC_ERR_GRID_OVERFLOW at plan creation).
+ *   - Both polarisations share one GCF (no polarisation mixing).
+ *   - Device pointers must come from cudaMalloc (or torch) on the device that is
+ *     current when the plan is created; host pointers are plain host memory.
+ *   - Calls are stream-ordered and asynchronous unless stated; CUDA errors of
+ *     kernels surface as EPIC_ERR_CUDA from a later call or from epic_sync.
+ *   - No CPU fallback: without a usable sm_103a GPU, plan creation fails.
+ */
+#ifndef EPIC_H
+#define EPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EPIC_OK = 0,
+    EPIC_ERR_INVALID_ARG = 1,   /* bad size, pointer, flag or descriptor field; nothing launched */
+    EPIC_ERR_GRID_OVERFLOW = 2, /* a GCF tap falls outside the N x N grid (plan creation)        */
+    EPIC_ERR_OOM = 3,           /* device or host allocation failed, or a server memory limit    */
+    EPIC_ERR_BUSY = 4,          /* server: no free slot or memory now; retry later               */
+    EPIC_ERR_TIMEOUT = 5,       /* a bounded wait ran out                                         */
+    EPIC_ERR_CUDA = 6,          /* a CUDA call failed; epic_last_error() has the text             */
+    EPIC_ERR_UNSUPPORTED = 7,   /* valid request this build cannot run (e.g. path/size combo)    */
+    EPIC_ERR_NOT_FOUND = 8      /* unknown server ticket                                          */
+} epic_status;
+
+/* Which implementation of the hot path a plan uses. */
+typedef enum {
+    EPIC_PATH_PLAIN_FP32 = 0,   /* unfused FP32: grid kernel -> HBM -> row FFT -> HBM -> column FFT
+                                   -> HBM -> square/accumulate kernel (the plain comparator)      */
+    EPIC_PATH_FUSED_FP32 = 1,   /* one fused kernel per block: grid -> FP32 FFT -> products ->
+                                   on-chip accumulation, images written once                      */
+    EPIC_PATH_DFTGEMM_FP16 = 2, /* fused kernel with the 2-D transform as two DFT-as-GEMM stages on
+                                   the tcgen05 tensor cores: FP16 operands, FP32 accumulation     */
+    EPIC_PATH_AUTO = 3          /* pick per plan (measured choice when a tuning entry exists)     */
+} epic_path;
+
+typedef enum {
+    EPIC_GCF_GAUSSIAN = 0,      /* W(d) = exp(-|d|^2 / (2 sigma_c^2)), d in cells, not renormalised */
+    EPIC_GCF_TABLE = 1          /* complex W sampled on a (K*os+1)^2 table, nearest sample        */
+} epic_gcf_kind;
+
+/* Gridding convolution function (Eq. 1: W_e^{ap}(r_j - r_e), here one W for all
+ * elements and both polarisations; the conjugate W* is what multiplies E). */
+typedef struct {
+    int kind;               /* epic_gcf_kind                                                      */
+    int K;                  /* taps per side, 1..8 (2 = the paper's 2x2 kernel, Sec. 4)           */
+    double sigma_cells;     /* GAUSSIAN: sigma in grid cells at f_ref_hz                          */
+    double f_ref_hz;        /* GAUSSIAN: reference frequency of sigma                             */
+    int freq_scaled;        /* GAUSSIAN: nonzero -> sigma_c = sigma_cells * f_c / f_ref_hz        */
+    int oversample;         /* TABLE: samples per cell os >= 1                                    */
+    const float* table;     /* TABLE: host, complex float pairs [(K*os+1)][(K*os+1)]; sample
+                               (iy, ix) is W at offset (ix/os - K/2, iy/os - K/2) cells; copied   */
+} epic_gcf_desc;
+
+/* Everything epic_image needs besides the voltages (Eq. 1: element positions r_e,
+ * grid r_j, kernel W; Eq. 2: polarisations).  All host arrays are copied. */
+typedef struct {
+    int n_ant;              /* elements A >= 1                                                    */
+    const double* pos_m;    /* host [n_ant][2] x, y in metres                                     */
+    int n_pol;              /* 1 or 2                                                             */
+    int n_chan;             /* channels C >= 1                                                    */
+    const double* freq_hz;  /* host [n_chan] centre frequency of each channel, > 0                */
+    const double* cell_m;   /* host [n_chan] grid spacing Delta_c, or NULL for lambda_c / 2       */
+    int grid_n;             /* N: power of two, 8..256                                            */
+    epic_gcf_desc gcf;
+    int path;               /* epic_path                                                          */
+    int max_time;           /* largest T of one call (sizes scratch and host staging), >= 1       */
+} epic_plan_desc;
+
+typedef struct epic_plan_s* epic_plan_t;
+
+/* What a plan resolved to (for logging and roofline bookkeeping). */
+typedef struct {
+    int path;               /* the epic_path actually used (never EPIC_PATH_AUTO)                 */
+    int n_prod;             /* 1 or 4                                                             */
+    int box_max_x;          /* largest occupied-grid width over channels (cells)                  */
+    int box_max_y;          /* largest occupied-grid height over channels (cells)                 */
+    int time_chunk;         /* time samples per internal pass                                     */
+    size_t device_bytes;    /* device memory owned by the plan                                    */
+    size_t scratch_bytes;   /* part of device_bytes used as per-call scratch                      */
+    int n_kernels;          /* kernels in one epic_image call for T = max_time                    */
+} epic_plan_info;
+
+/* flags of epic_image / epic_image_host */
+#define EPIC_RESET       0u /* out = images of this block                                         */
+#define EPIC_ACCUMULATE  1u /* out += images of this block (continue an integration / resume)     */
+#define EPIC_TIME_KERNELS 2u /* record CUDA events around each kernel (see epic_kernel_times)     */
+
+/* Build a plan: geometry and GCF taps in FP64 on the host (Eq. 1 bracket), the
+ * inverse cell -> (element, weight) lists, transform tables, device uploads.
+ * Returns EPIC_ERR_INVALID_ARG for a bad descriptor, EPIC_ERR_GRID_OVERFLOW if a
+ * footprint leaves the grid, EPIC_ERR_UNSUPPORTED for a path this build cannot
+ * run at these sizes, EPIC_ERR_CUDA / EPIC_ERR_OOM on device failure.  On error
+ * *out is NULL and nothing is leaked.  The plan owns all its device memory. */
+epic_status epic_plan_create(const epic_plan_desc* desc, epic_plan_t* out);
+
+/* Free a plan and its device memory (synchronises the plan's last stream). NULL is OK. */
+epic_status epic_plan_destroy(epic_plan_t plan);
+
+/* Image one voltage block (Eq. 1-2) on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  volt: device uint8[T][C][A][P]; out: device float32
+ * [C][n_prod][N][N], written (EPIC_RESET) or added to (EPIC_ACCUMULATE).
+ * 0 <= T <= max_time; T = 0 with EPIC_RESET zeroes out.  Asynchronous: returns
+ * after launching.  The plan's scratch is reused by every call, so calls on one
+ * plan must not overlap on different streams. */
+epic_status epic_image(epic_plan_t plan, const uint8_t* volt, int T, void* stream, float* out,
+                       unsigned flags);
+
+/* Same as epic_image with HOST buffers: copies volt_host (T*C*A*P bytes) to the
+ * plan's device staging buffer, images it, copies the images to out_host
+ * (C*n_prod*N*N floats; with EPIC_ACCUMULATE its old content is uploaded first)
+ * and synchronises the stream before returning.  Pinned host memory is fastest. */
+epic_status epic_image_host(epic_plan_t plan, const uint8_t* volt_host, int T, void* stream,
+                            float* out_host, unsigned flags);
+
+/* Wait for the plan's last stream and report any asynchronous CUDA error. */
+epic_status epic_sync(epic_plan_t plan);
+
+/* Kernel durations (ms) of the last call made with EPIC_TIME_KERNELS, in launch
+ * order, with static kernel names.  Synchronises on the recorded events.
+ * *n_out = number of kernels (<= max entries are written). */
+epic_status epic_kernel_times(epic_plan_t plan, const char** names, float* ms, int max, int* n_out);
+
+epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
+
+/* Static text of a status code, and the detail of the last error on a plan
+ * (or of the last failed epic_plan_create when plan is NULL).  Never NULL. */
+const char* epic_status_str(epic_status s);
+const char* epic_last_error(epic_plan_t plan);
+
+/* Library and device facts: SM count and opt-in shared memory of the current
+ * device; returns EPIC_ERR_CUDA without a usable device. */
+epic_status epic_device_query(int* sm_count, int* smem_optin_bytes, int* cc_major, int* cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPIC_H */

@@ -1,0 +1,428 @@
+// C ABI of libepic.so: argument checking, plan lifetime, device uploads,
+// dispatch to the path kernels, host-buffer convenience call, kernel timing.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "epic_internal.h"
+
+namespace {
+std::mutex g_err_mu;
+std::string g_create_error;  // detail of the last failed epic_plan_create
+
+void set_create_error(const std::string& s)
+{
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_error = s;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const T* src, size_t n, size_t* bytes)
+{
+    *dst = nullptr;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    *bytes += n * sizeof(T);
+    return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_plan(epic_plan_s* p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->dt.box);
+    cudaFree(p->dt.cell_off);
+    cudaFree(p->dt.cell_ptr);
+    cudaFree(p->dt.contrib_e);
+    cudaFree(p->dt.contrib_w);
+    cudaFree(p->dt.twiddle);
+    cudaFree(p->dt.first_xy);
+    cudaFree(p->dt.w_taps);
+    cudaFree(p->dt.dft_f16);
+    cudaFree(p->scratch);
+    cudaFree(p->stage_volt);
+    cudaFree(p->stage_out);
+    for (auto& ev : p->events) {
+        cudaEventDestroy(ev.start);
+        cudaEventDestroy(ev.stop);
+    }
+    cudaSetDevice(cur);
+    delete p;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+}  // namespace
+
+namespace epic {
+
+epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (p) p->last_error = msg;
+    set_create_error(msg);
+    return e == cudaErrorMemoryAllocation ? EPIC_ERR_OOM : EPIC_ERR_CUDA;
+}
+
+void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s)
+{
+    if (!p->timing) return;
+    if (p->n_events == p->events.size()) {
+        if (p->events.size() >= 8192) return;
+        KernelEvent ev{name, nullptr, nullptr};
+        cudaEventCreate(&ev.start);
+        cudaEventCreate(&ev.stop);
+        p->events.push_back(ev);
+    }
+    p->events[p->n_events].name = name;
+    cudaEventRecord(p->events[p->n_events].start, s);
+}
+
+void ev_end(epic_plan_s* p, cudaStream_t s)
+{
+    if (!p->timing || p->n_events >= p->events.size()) return;
+    cudaEventRecord(p->events[p->n_events].stop, s);
+    ++p->n_events;
+}
+
+}  // namespace epic
+
+extern "C" {
+
+const char* epic_status_str(epic_status s)
+{
+    switch (s) {
+        case EPIC_OK: return "EPIC_OK";
+        case EPIC_ERR_INVALID_ARG: return "EPIC_ERR_INVALID_ARG";
+        case EPIC_ERR_GRID_OVERFLOW: return "EPIC_ERR_GRID_OVERFLOW";
+        case EPIC_ERR_OOM: return "EPIC_ERR_OOM";
+        case EPIC_ERR_BUSY: return "EPIC_ERR_BUSY";
+        case EPIC_ERR_TIMEOUT: return "EPIC_ERR_TIMEOUT";
+        case EPIC_ERR_CUDA: return "EPIC_ERR_CUDA";
+        case EPIC_ERR_UNSUPPORTED: return "EPIC_ERR_UNSUPPORTED";
+        case EPIC_ERR_NOT_FOUND: return "EPIC_ERR_NOT_FOUND";
+    }
+    return "EPIC_ERR_UNKNOWN";
+}
+
+const char* epic_last_error(epic_plan_t plan)
+{
+    if (plan) return plan->last_error.c_str();
+    static thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    copy = g_create_error;
+    return copy.c_str();
+}
+
+epic_status epic_device_query(int* sm_count, int* smem_optin_bytes, int* cc_major, int* cc_minor)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return epic::cuda_fail(nullptr, e, "cudaGetDevice");
+    int v = 0;
+    if (sm_count) {
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return epic::cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+        *sm_count = v;
+    }
+    if (smem_optin_bytes) {
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return epic::cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+        *smem_optin_bytes = v;
+    }
+    if (cc_major) {
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, dev);
+        if (e != cudaSuccess) return epic::cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+        *cc_major = v;
+    }
+    if (cc_minor) {
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev);
+        if (e != cudaSuccess) return epic::cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+        *cc_minor = v;
+    }
+    return EPIC_OK;
+}
+
+epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
+{
+    if (!out) {
+        set_create_error("out pointer is NULL");
+        return EPIC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    auto bad = [](const char* why) {
+        set_create_error(why);
+        return EPIC_ERR_INVALID_ARG;
+    };
+    if (!d) return bad("descriptor is NULL");
+    if (d->n_ant < 1 || !d->pos_m) return bad("n_ant must be >= 1 and pos_m non-NULL");
+    if (d->n_pol != 1 && d->n_pol != 2) return bad("n_pol must be 1 or 2");
+    if (d->n_chan < 1 || !d->freq_hz) return bad("n_chan must be >= 1 and freq_hz non-NULL");
+    if (!is_pow2(d->grid_n) || d->grid_n < 8 || d->grid_n > 256) return bad("grid_n must be a power of two in 8..256");
+    if (d->max_time < 1) return bad("max_time must be >= 1");
+    if (d->gcf.K < 1 || d->gcf.K > 8 || d->gcf.K > d->grid_n) return bad("gcf.K must be in 1..8");
+    if (d->gcf.kind == EPIC_GCF_GAUSSIAN) {
+        if (!(d->gcf.sigma_cells > 0.0) || !std::isfinite(d->gcf.sigma_cells)) return bad("gcf.sigma_cells must be > 0");
+        if (d->gcf.freq_scaled && !(d->gcf.f_ref_hz > 0.0)) return bad("gcf.f_ref_hz must be > 0 when freq_scaled");
+    } else if (d->gcf.kind == EPIC_GCF_TABLE) {
+        if (d->gcf.oversample < 1 || d->gcf.oversample > 1024 || !d->gcf.table)
+            return bad("TABLE GCF needs oversample in 1..1024 and a table");
+    } else {
+        return bad("unknown gcf.kind");
+    }
+    if (d->path < EPIC_PATH_PLAIN_FP32 || d->path > EPIC_PATH_AUTO) return bad("unknown path");
+    if ((long long)d->n_ant * d->n_pol > (1 << 20)) return bad("n_ant * n_pol too large");
+    for (int c = 0; c < d->n_chan; ++c) {
+        if (!(d->freq_hz[c] > 0.0) || !std::isfinite(d->freq_hz[c])) return bad("freq_hz must be > 0 and finite");
+        if (d->cell_m && (!(d->cell_m[c] > 0.0) || !std::isfinite(d->cell_m[c]))) return bad("cell_m must be > 0");
+    }
+    for (int i = 0; i < 2 * d->n_ant; ++i)
+        if (!std::isfinite(d->pos_m[i])) return bad("pos_m must be finite");
+
+    epic_plan_s* p = new (std::nothrow) epic_plan_s();
+    if (!p) {
+        set_create_error("host allocation failed");
+        return EPIC_ERR_OOM;
+    }
+    p->A = d->n_ant;
+    p->P = d->n_pol;
+    p->C = d->n_chan;
+    p->N = d->grid_n;
+    p->K = d->gcf.K;
+    p->nprod = d->n_pol == 1 ? 1 : 4;
+    p->max_time = d->max_time;
+    p->logN = 0;
+    while ((1 << p->logN) < p->N) ++p->logN;
+    p->pos.assign(d->pos_m, d->pos_m + 2 * (size_t)d->n_ant);
+    p->freq.assign(d->freq_hz, d->freq_hz + d->n_chan);
+    if (d->cell_m) p->cell.assign(d->cell_m, d->cell_m + d->n_chan);
+    p->gcf = d->gcf;
+    if (d->gcf.kind == EPIC_GCF_TABLE) {
+        const size_t side = (size_t)d->gcf.K * d->gcf.oversample + 1;
+        p->table.assign(d->gcf.table, d->gcf.table + 2 * side * side);
+    }
+    p->gcf.table = nullptr;
+
+    std::string err;
+    epic_status st = epic::build_geometry(p, &err);
+    if (st != EPIC_OK) {
+        set_create_error(err);
+        delete p;
+        return st;
+    }
+
+    // device: must be a GB300-class (sm_103) part; this library carries sm_103a code only
+    int major = 0, minor = 0;
+    st = epic_device_query(&p->sm_count, &p->smem_optin, &major, &minor);
+    if (st != EPIC_OK) {
+        delete p;
+        return st;
+    }
+    cudaGetDevice(&p->device);
+    if (!(major == 10 && minor == 3)) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device has compute capability %d.%d; this build carries sm_103a code only", major,
+                 minor);
+        set_create_error(buf);
+        delete p;
+        return EPIC_ERR_UNSUPPORTED;
+    }
+
+    int path = d->path;
+    if (path == EPIC_PATH_AUTO) path = EPIC_PATH_DFTGEMM_FP16;
+    p->path = path;
+
+    // shared device tables
+    std::vector<int> cell_off, cell_ptr, contrib_e;
+    std::vector<float2> contrib_w, tw;
+    epic::build_csr(p, cell_off, cell_ptr, contrib_e, contrib_w);
+    epic::build_twiddles(p->N, tw);
+    std::vector<int4> box(p->C);
+    for (int c = 0; c < p->C; ++c) box[c] = make_int4(p->box[c].x0, p->box[c].y0, p->box[c].nx, p->box[c].ny);
+    std::vector<int> first_xy((size_t)p->C * p->A);
+    for (size_t i = 0; i < first_xy.size(); ++i) first_xy[i] = (p->first_y[i] << 16) | p->first_x[i];
+    std::vector<float2> w_taps(p->w_re.size());
+    for (size_t i = 0; i < w_taps.size(); ++i) w_taps[i] = make_float2((float)p->w_re[i], (float)p->w_im[i]);
+
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = upload(&p->dt.box, box.data(), box.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.cell_off, cell_off.data(), cell_off.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.cell_ptr, cell_ptr.data(), cell_ptr.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.contrib_e, contrib_e.data(), contrib_e.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.contrib_w, contrib_w.data(), contrib_w.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.twiddle, tw.data(), tw.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.first_xy, first_xy.data(), first_xy.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.w_taps, w_taps.data(), w_taps.size(), &p->table_bytes);
+    if (e != cudaSuccess) {
+        st = epic::cuda_fail(p, e, "plan table upload");
+        free_plan(p);
+        return st;
+    }
+
+    switch (p->path) {
+        case EPIC_PATH_PLAIN_FP32: st = epic::plain_setup(p); break;
+        case EPIC_PATH_FUSED_FP32: st = epic::fused_setup(p); break;
+        case EPIC_PATH_DFTGEMM_FP16: st = epic::dftgemm_setup(p); break;
+        default: st = EPIC_ERR_INVALID_ARG;
+    }
+    if (st != EPIC_OK) {
+        set_create_error(p->last_error);
+        free_plan(p);
+        return st;
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        st = epic::cuda_fail(p, e, "plan setup");
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return EPIC_OK;
+}
+
+epic_status epic_plan_destroy(epic_plan_t plan)
+{
+    free_plan(plan);
+    return EPIC_OK;
+}
+
+epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
+{
+    if (!p || !info) return EPIC_ERR_INVALID_ARG;
+    info->path = p->path;
+    info->n_prod = p->nprod;
+    info->box_max_x = p->box_max_x;
+    info->box_max_y = p->box_max_y;
+    info->time_chunk = p->time_chunk;
+    info->scratch_bytes = p->scratch_bytes;
+    info->device_bytes = p->table_bytes + p->scratch_bytes + p->dt.dft_bytes + p->stage_bytes;
+    int nk = 0;
+    const int chunks = p->time_chunk > 0 ? (p->max_time + p->time_chunk - 1) / p->time_chunk : 1;
+    if (p->path == EPIC_PATH_PLAIN_FP32) nk = 4 * chunks;
+    else nk = p->scratch ? 2 : 1;
+    info->n_kernels = nk;
+    return EPIC_OK;
+}
+
+static epic_status image_impl(epic_plan_t p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
+{
+    const bool acc = (flags & EPIC_ACCUMULATE) != 0;
+    p->timing = (flags & EPIC_TIME_KERNELS) != 0;
+    p->n_events = 0;
+    p->last_stream = s;
+    if (T == 0) {
+        if (!acc) {
+            cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)p->C * p->nprod * p->N * p->N, s);
+            if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemsetAsync(out)");
+        }
+        return EPIC_OK;
+    }
+    switch (p->path) {
+        case EPIC_PATH_PLAIN_FP32: return epic::plain_run(p, volt, T, s, out, acc);
+        case EPIC_PATH_FUSED_FP32: return epic::fused_run(p, volt, T, s, out, acc);
+        case EPIC_PATH_DFTGEMM_FP16: return epic::dftgemm_run(p, volt, T, s, out, acc);
+    }
+    return EPIC_ERR_INVALID_ARG;
+}
+
+epic_status epic_image(epic_plan_t p, const uint8_t* volt, int T, void* stream, float* out, unsigned flags)
+{
+    if (!p) return EPIC_ERR_INVALID_ARG;
+    if (T < 0 || T > p->max_time) {
+        p->last_error = "T must be in 0..max_time";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    if (!out || (T > 0 && !volt)) {
+        p->last_error = "NULL voltage or image pointer";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)) {
+        p->last_error = "unknown flag bits";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    cudaPointerAttributes at{};
+    auto on_device = [&](const void* ptr) {
+        return cudaPointerGetAttributes(&at, ptr) == cudaSuccess &&
+               (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    };
+    if (!on_device(out) || (T > 0 && !on_device(volt))) {
+        cudaGetLastError();
+        p->last_error = "voltage and image pointers must be device memory";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    return image_impl(p, volt, T, (cudaStream_t)stream, out, flags);
+}
+
+epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void* stream, float* out_host,
+                            unsigned flags)
+{
+    if (!p) return EPIC_ERR_INVALID_ARG;
+    if (T < 0 || T > p->max_time || !out_host || (T > 0 && !volt_host)) {
+        p->last_error = "bad T or NULL host pointer";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)) {
+        p->last_error = "unknown flag bits";
+        return EPIC_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vb = (size_t)p->max_time * p->C * p->A * p->P;
+    const size_t ob = sizeof(float) * (size_t)p->C * p->nprod * p->N * p->N;
+    if (!p->stage_volt) {
+        cudaError_t e = cudaMalloc(&p->stage_volt, vb);
+        if (e == cudaSuccess) e = cudaMalloc(&p->stage_out, ob);
+        if (e != cudaSuccess) {
+            cudaFree(p->stage_volt);
+            p->stage_volt = nullptr;
+            return epic::cuda_fail(p, e, "cudaMalloc(host-call staging)");
+        }
+        p->stage_bytes = vb + ob;
+    }
+    const size_t tb = (size_t)T * p->C * p->A * p->P;
+    cudaError_t e = cudaSuccess;
+    if (tb) e = cudaMemcpyAsync(p->stage_volt, volt_host, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && (flags & EPIC_ACCUMULATE))
+        e = cudaMemcpyAsync(p->stage_out, out_host, ob, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemcpyAsync(H2D)");
+    epic_status st = image_impl(p, p->stage_volt, T, s, p->stage_out, flags);
+    if (st != EPIC_OK) return st;
+    e = cudaMemcpyAsync(out_host, p->stage_out, ob, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemcpyAsync(D2H)");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaStreamSynchronize");
+    return EPIC_OK;
+}
+
+epic_status epic_sync(epic_plan_t p)
+{
+    if (!p) return EPIC_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "epic_sync");
+    return EPIC_OK;
+}
+
+epic_status epic_kernel_times(epic_plan_t p, const char** names, float* ms, int max, int* n_out)
+{
+    if (!p || !n_out || max < 0) return EPIC_ERR_INVALID_ARG;
+    *n_out = (int)p->n_events;
+    for (size_t i = 0; i < p->n_events && (int)i < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(p->events[i].stop);
+        if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p->events[i].start, p->events[i].stop);
+        if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaEventElapsedTime");
+        if (names) names[i] = p->events[i].name;
+        if (ms) ms[i] = t;
+    }
+    return EPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the host plan, the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/epic.h"
+
+namespace epic {
+
+// Occupied part of one channel's grid: every GCF tap of every element lies in
+// rows [y0, y0+ny) and columns [x0, x0+nx).
+struct Box {
+    int x0, y0, nx, ny;
+};
+
+// Device tables of one plan (all channels concatenated).
+struct DeviceTables {
+    int4* box = nullptr;          // [C] (x0, y0, nx, ny)
+    int* cell_off = nullptr;      // [C+1] offset of channel c's first cell in cell_ptr
+    int* cell_ptr = nullptr;      // per channel nx*ny+1 offsets (absolute into contrib arrays)
+    int* contrib_e = nullptr;     // element of each (cell, element) contribution
+    float2* contrib_w = nullptr;  // conj(W) * (-1)^(x+y) of each contribution
+    float2* twiddle = nullptr;    // [N/2] exp(+2 pi i m / N)
+    int* first_xy = nullptr;      // [C][A] packed first tap (y << 16 | x)
+    float2* w_taps = nullptr;     // [C][A][K][K] weights (conj, shift sign folded)
+    uint16_t* dft_f16 = nullptr;  // DFT-as-GEMM operand tables (tensor path)
+    size_t dft_bytes = 0;
+};
+
+struct KernelEvent {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace epic
+
+struct epic_plan_s {
+    // descriptor copy
+    int A = 0, P = 0, C = 0, N = 0, K = 0, nprod = 0, path = 0, max_time = 0;
+    int logN = 0;
+    int device = 0;
+    std::vector<double> pos, freq, cell;
+    epic_gcf_desc gcf{};
+    std::vector<float> table;
+
+    // host geometry (FP64 computed, stored as used by the kernels)
+    std::vector<epic::Box> box;           // [C]
+    std::vector<int> first_x, first_y;    // [C][A]
+    std::vector<double> w_re, w_im;       // [C][A][K][K], conj(W) * (-1)^(jx+jy)
+    int box_max_x = 0, box_max_y = 0;
+    size_t n_contrib = 0;
+
+    // device state
+    epic::DeviceTables dt;
+    size_t table_bytes = 0;
+    void* scratch = nullptr;              // path-specific per-call scratch
+    size_t scratch_bytes = 0;
+    int time_chunk = 0;
+    uint8_t* stage_volt = nullptr;        // host-API staging
+    float* stage_out = nullptr;
+    size_t stage_bytes = 0;
+    int sm_count = 0;
+    int smem_optin = 0;
+    int fused_variant = 0;                // kernel variant chosen for fused paths
+    int slab = 0;                         // output columns per work item (fused paths)
+
+    // errors / timing
+    std::string last_error;
+    cudaStream_t last_stream = nullptr;
+    bool timing = false;
+    std::vector<epic::KernelEvent> events;
+    size_t n_events = 0;
+};
+
+namespace epic {
+
+// plan.cpp
+epic_status build_geometry(epic_plan_s* p, std::string* err);
+void build_csr(const epic_plan_s* p, std::vector<int>& cell_off, std::vector<int>& cell_ptr,
+               std::vector<int>& contrib_e, std::vector<float2>& contrib_w);
+void build_twiddles(int N, std::vector<float2>& tw);
+
+// api.cu helpers used by the kernels' launch code
+void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s);
+void ev_end(epic_plan_s* p, cudaStream_t s);
+epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);
+
+// k_plain.cu
+epic_status plain_setup(epic_plan_s* p);
+epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+
+// k_fused.cu
+epic_status fused_setup(epic_plan_s* p);
+epic_status fused_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+
+// k_dftgemm.cu
+epic_status dftgemm_setup(epic_plan_s* p);
+epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+
+}  // namespace epic

@@ -1,0 +1,61 @@
+// Small device helpers shared by the EPIC kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace epic {
+
+// One packed voltage byte -> complex float: real = high nibble, imaginary = low
+// nibble, both 4-bit two's complement (sign-extended by arithmetic shifts).
+__device__ __forceinline__ float2 unpack44(uint32_t b)
+{
+    const int re = ((int)(b << 24)) >> 28;
+    const int im = ((int)(b << 28)) >> 28;
+    return make_float2((float)re, (float)im);
+}
+
+// acc + w * v for complex numbers.
+__device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc)
+{
+    acc.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, acc.x));
+    acc.y = fmaf(w.x, v.y, fmaf(w.y, v.x, acc.y));
+    return acc;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Radix-2 Stockham autosort FFT with the + sign (Eq. 1), unnormalised, on
+// `batch` transforms of length n = 2^logn held in shared memory: element i of
+// transform q is buf[q * bs + i * es].  Ping-pongs between a and b; returns the
+// buffer holding the natural-order result.  tw[m] = exp(+2 pi i m / n), m < n/2.
+// Ends with __syncthreads(); all threads of the block must call it.
+__device__ __forceinline__ float2* fft_stockham_r2(float2* a, float2* b, int logn, int batch, int es, int bs,
+                                                   const float2* tw)
+{
+    const int half = 1 << (logn - 1);
+    __syncthreads();
+    for (int s = 0; s < logn; ++s) {
+        const int Ns = 1 << s;
+        for (int w = threadIdx.x; w < batch * half; w += blockDim.x) {
+            const int q = w >> (logn - 1);
+            const int j = w & (half - 1);
+            const int k = j & (Ns - 1);
+            const float2 v0 = a[q * bs + j * es];
+            const float2 v1 = cmul(a[q * bs + (j + half) * es], tw[k << (logn - 1 - s)]);
+            const int idx = ((j >> s) << (s + 1)) + k;
+            b[q * bs + idx * es] = make_float2(v0.x + v1.x, v0.y + v1.y);
+            b[q * bs + (idx + Ns) * es] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        }
+        __syncthreads();
+        float2* t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+}  // namespace epic

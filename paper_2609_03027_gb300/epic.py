@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libepic.so (include/epic.h).
+
+Argument marshalling only: every step of the imaging path runs in the CUDA
+library.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library cannot be built or loaded, or the device is not an
+sm_103 GPU, these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import buildlib as _build
+
+PATH_PLAIN_FP32 = 0
+PATH_FUSED_FP32 = 1
+PATH_DFTGEMM_FP16 = 2
+PATH_AUTO = 3
+PATHS = {"plain": PATH_PLAIN_FP32, "fused": PATH_FUSED_FP32, "dftgemm": PATH_DFTGEMM_FP16, "auto": PATH_AUTO}
+PATH_NAMES = {v: k for k, v in PATHS.items()}
+
+GCF_GAUSSIAN = 0
+GCF_TABLE = 1
+
+RESET = 0
+ACCUMULATE = 1
+TIME_KERNELS = 2
+
+STATUS = {0: "EPIC_OK", 1: "EPIC_ERR_INVALID_ARG", 2: "EPIC_ERR_GRID_OVERFLOW", 3: "EPIC_ERR_OOM",
+          4: "EPIC_ERR_BUSY", 5: "EPIC_ERR_TIMEOUT", 6: "EPIC_ERR_CUDA", 7: "EPIC_ERR_UNSUPPORTED",
+          8: "EPIC_ERR_NOT_FOUND"}
+
+# Every symbol declared in include/epic.h (checked by the ABI tests).
+EXPORTED = ["epic_plan_create", "epic_plan_destroy", "epic_image", "epic_image_host", "epic_sync",
+            "epic_kernel_times", "epic_plan_get_info", "epic_status_str", "epic_last_error",
+            "epic_device_query"]
+
+
+class EpicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Gcf(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("K", ctypes.c_int), ("sigma_cells", ctypes.c_double),
+                ("f_ref_hz", ctypes.c_double), ("freq_scaled", ctypes.c_int), ("oversample", ctypes.c_int),
+                ("table", ctypes.POINTER(ctypes.c_float))]
+
+
+class _PlanDesc(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("pos_m", ctypes.POINTER(ctypes.c_double)), ("n_pol", ctypes.c_int),
+                ("n_chan", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_double)),
+                ("cell_m", ctypes.POINTER(ctypes.c_double)), ("grid_n", ctypes.c_int), ("gcf", _Gcf),
+                ("path", ctypes.c_int), ("max_time", ctypes.c_int)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("n_prod", ctypes.c_int), ("box_max_x", ctypes.c_int),
+                ("box_max_y", ctypes.c_int), ("time_chunk", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+                ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libepic.so (building it first if absent or stale when nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libepic.so not found at {path}; run paper_2609_03027_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp, i, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+        L.epic_plan_create.argtypes = [P(_PlanDesc), P(vp)]
+        L.epic_plan_destroy.argtypes = [vp]
+        L.epic_image.argtypes = [vp, vp, i, vp, vp, u]
+        L.epic_image_host.argtypes = [vp, vp, i, vp, vp, u]
+        L.epic_sync.argtypes = [vp]
+        L.epic_kernel_times.argtypes = [vp, P(ctypes.c_char_p), P(ctypes.c_float), i, P(i)]
+        L.epic_plan_get_info.argtypes = [vp, P(_PlanInfo)]
+        L.epic_status_str.argtypes = [i]
+        L.epic_status_str.restype = ctypes.c_char_p
+        L.epic_last_error.argtypes = [vp]
+        L.epic_last_error.restype = ctypes.c_char_p
+        L.epic_device_query.argtypes = [P(i), P(i), P(i), P(i)]
+        for name in EXPORTED:
+            if name not in ("epic_status_str", "epic_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(L, st: int, plan=None):
+    if st != 0:
+        msg = L.epic_last_error(plan).decode(errors="replace")
+        raise EpicError(st, msg)
+
+
+def device_query() -> Dict[str, int]:
+    L = load()
+    a, b, c, d = (ctypes.c_int() for _ in range(4))
+    _check(L, L.epic_device_query(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return {"sm_count": a.value, "smem_optin": b.value, "cc_major": c.value, "cc_minor": d.value}
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """An imaging plan: geometry, GCF taps and tables resident on the current GPU.
+
+    ``path`` is one of "plain", "fused", "dftgemm", "auto".
+    """
+
+    def __init__(self, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int, sigma_cells: float = 1.0,
+                 f_ref_hz: Optional[float] = None, freq_scaled: bool = False, cell_m=None, path: str = "auto",
+                 max_time: int = 1024, gcf_table=None, oversample: int = 1):
+        self._lib = load()
+        self.pos = np.ascontiguousarray(pos_m, dtype=np.float64).reshape(-1, 2)
+        self.freq = np.ascontiguousarray(freq_hz, dtype=np.float64).ravel()
+        self.cell = None if cell_m is None else np.ascontiguousarray(cell_m, dtype=np.float64).ravel()
+        self.table = None if gcf_table is None else np.ascontiguousarray(gcf_table, dtype=np.float32).ravel()
+        self.n_ant, self.n_chan, self.n_pol, self.grid_n = self.pos.shape[0], self.freq.shape[0], int(n_pol), int(grid_n)
+        self.n_prod = 1 if self.n_pol == 1 else 4
+        self.max_time = int(max_time)
+        d = _PlanDesc()
+        d.n_ant = self.n_ant
+        d.pos_m = self.pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_pol = self.n_pol
+        d.n_chan = self.n_chan
+        d.freq_hz = self.freq.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.cell_m = None if self.cell is None else self.cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.grid_n = self.grid_n
+        d.gcf.kind = GCF_GAUSSIAN if self.table is None else GCF_TABLE
+        d.gcf.K = int(gcf_k)
+        d.gcf.sigma_cells = float(sigma_cells)
+        d.gcf.f_ref_hz = float(f_ref_hz if f_ref_hz is not None else self.freq.max())
+        d.gcf.freq_scaled = int(bool(freq_scaled))
+        d.gcf.oversample = int(oversample)
+        d.gcf.table = None if self.table is None else self.table.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d.path = PATHS[path] if isinstance(path, str) else int(path)
+        d.max_time = self.max_time
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.epic_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_config(cls, cfg, path: str = "auto", max_time: Optional[int] = None) -> "Plan":
+        return cls(cfg.pos_m, cfg.freq_hz, cfg.n_pol, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells, cfg.f_ref_hz,
+                   cfg.freq_scaled, None, path, cfg.n_time if max_time is None else max_time)
+
+    # ------------------------------------------------------------------ calls
+    def _handle(self):
+        if self._h is None or not self._h.value:
+            raise EpicError(1, "plan is closed")
+        return self._h
+
+    def image(self, volt, out=None, accumulate: bool = False, stream=None, time_kernels: bool = False):
+        """Images of a device voltage block uint8[T][C][A][P] -> float32[C][n_prod][N][N] (device)."""
+        import torch
+        if not (isinstance(volt, torch.Tensor) and volt.is_cuda and volt.dtype == torch.uint8):
+            raise TypeError("volt must be a CUDA uint8 tensor [T][C][A][P]")
+        if not volt.is_contiguous() or volt.dim() != 4 or tuple(volt.shape[1:]) != (self.n_chan, self.n_ant, self.n_pol):
+            raise ValueError(f"volt must be contiguous [T][{self.n_chan}][{self.n_ant}][{self.n_pol}]")
+        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=volt.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+            raise ValueError(f"out must be a contiguous CUDA float32 tensor {shape}")
+        flags = (ACCUMULATE if accumulate else RESET) | (TIME_KERNELS if time_kernels else 0)
+        T = int(volt.shape[0])
+        st = self._lib.epic_image(self._handle(), volt.data_ptr() if T else None, T, _stream_handle(stream),
+                                  out.data_ptr(), flags)
+        _check(self._lib, st, self._h)
+        return out
+
+    def image_host(self, volt: np.ndarray, out: Optional[np.ndarray] = None, accumulate: bool = False,
+                   stream=None, time_kernels: bool = False) -> np.ndarray:
+        """Host-buffer call: H2D copy, imaging, D2H copy, stream synchronised on return."""
+        v = np.asarray(volt)
+        if v.dtype != np.uint8 or v.ndim != 4 or v.shape[1:] != (self.n_chan, self.n_ant, self.n_pol):
+            raise ValueError("volt must be uint8 [T][C][A][P]")
+        if not v.flags.c_contiguous:
+            raise ValueError("volt must be C-contiguous")
+        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        if out is None:
+            out = np.zeros(shape, dtype=np.float32)
+        if out.shape != shape or out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be C-contiguous float32 {shape}")
+        flags = (ACCUMULATE if accumulate else RESET) | (TIME_KERNELS if time_kernels else 0)
+        st = self._lib.epic_image_host(self._handle(), v.ctypes.data if v.shape[0] else None, int(v.shape[0]),
+                                       _stream_handle(stream), out.ctypes.data, flags)
+        _check(self._lib, st, self._h)
+        return out
+
+    def image_host_ptr(self, volt_ptr: int, T: int, out_ptr: int, accumulate: bool = False, stream=None):
+        """Host-buffer call on raw host pointers (e.g. pinned torch tensors)."""
+        flags = ACCUMULATE if accumulate else RESET
+        st = self._lib.epic_image_host(self._handle(), volt_ptr, int(T), _stream_handle(stream), out_ptr, flags)
+        _check(self._lib, st, self._h)
+
+    def sync(self):
+        _check(self._lib, self._lib.epic_sync(self._handle()), self._h)
+
+    def kernel_times(self) -> List[Tuple[str, float]]:
+        n = ctypes.c_int()
+        _check(self._lib, self._lib.epic_kernel_times(self._handle(), None, None, 0, ctypes.byref(n)), self._h)
+        k = n.value
+        names = (ctypes.c_char_p * max(k, 1))()
+        ms = (ctypes.c_float * max(k, 1))()
+        _check(self._lib, self._lib.epic_kernel_times(self._handle(), names, ms, k, ctypes.byref(n)), self._h)
+        return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+    def info(self) -> Dict[str, int]:
+        inf = _PlanInfo()
+        _check(self._lib, self._lib.epic_plan_get_info(self._handle(), ctypes.byref(inf)), self._h)
+        d = {f: getattr(inf, f) for f, _ in _PlanInfo._fields_}
+        d["path_name"] = PATH_NAMES.get(d["path"], str(d["path"]))
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.epic_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

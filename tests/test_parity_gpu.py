@@ -1,0 +1,166 @@
+"""GPU parity: every CUDA path against the FP64 CPU oracle, element by element.
+
+Small cases cover several tiles, ragged time chunks and the method's edge
+cases; the four fixed workloads run at full size in the launch configuration
+the benchmark times, with the oracle checking sampled channels (lowest and
+highest frequency, full integration).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import epic_synth as synth
+from gpu_common import GPU_PATHS, TOL, assert_parity, oracle_image
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2609_03027_gb300 as E  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+
+
+def run_gpu(cfg, volt, path, **kw):
+    with E.Plan.from_config(cfg, path=path, max_time=max(1, volt.shape[0])) as plan:
+        v = torch.from_numpy(volt).cuda()
+        out = plan.image(v, **kw)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+SMALL = {
+    # name: (A, C, P, N, K, T, extra)
+    "dual-pol-ragged": (40, 3, 2, 64, 3, 37, {}),
+    "single-pol": (25, 2, 1, 32, 3, 19, {}),
+    "paper-2x2-gcf": (30, 2, 2, 32, 2, 11, {}),
+    "k1-point-gcf": (12, 2, 2, 16, 1, 7, {}),
+    "k5-freq-scaled": (50, 4, 2, 64, 5, 9, {"freq_scaled": True}),
+    "k7-wide": (64, 2, 2, 128, 7, 5, {}),
+    "n8-smallest": (6, 2, 2, 8, 3, 5, {"diameter_m": 3.0}),
+    "n256-largest": (300, 2, 2, 256, 3, 3, {"diameter_m": 60.0}),
+    "single-time-sample": (33, 3, 2, 32, 4, 1, {}),
+}
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+@pytest.mark.parametrize("case", list(SMALL))
+def test_small_cases_match_oracle(path, case):
+    A, C, P, N, K, T, extra = SMALL[case]
+    diam = extra.get("diameter_m", 0.28 * N)
+    cfg = synth.small_config(n_ant=A, n_chan=C, n_pol=P, grid_n=N, gcf_k=K, n_time=T, seed=100 + A,
+                             diameter_m=diam, freq_scaled=extra.get("freq_scaled", False), sigma=0.7)
+    v = synth.make_voltages(cfg)
+    got = run_gpu(cfg, v, path)
+    assert_parity(got, oracle_image(cfg, v), path, case)
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_every_byte_code_including_minus_eight(path):
+    cfg = synth.small_config(n_ant=64, n_chan=2, n_pol=2, grid_n=32, gcf_k=3, n_time=8, seed=7, diameter_m=9.0)
+    v = synth.random_bytes((8, 2, 64, 2), seed=3)
+    assert set(np.unique(v)) == set(range(256))
+    assert_parity(run_gpu(cfg, v, path), oracle_image(cfg, v), path, "all codes")
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_tabulated_complex_gcf(path):
+    K, os_ = 4, 8
+    cfg = synth.small_config(n_ant=30, n_chan=2, n_pol=2, grid_n=32, gcf_k=K, n_time=6, seed=17)
+    v = synth.make_voltages(cfg)
+    side = K * os_ + 1
+    s = np.arange(side) / os_ - K / 2.0
+    dy, dx = np.meshgrid(s, s, indexing="ij")
+    W = np.exp(-(dx ** 2 + 0.7 * dy ** 2) / 2) * np.exp(1j * (0.8 * dx - 0.5 * dy))
+    tab = np.stack([W.real, W.imag], -1).astype(np.float32)
+    import oracle
+    ref = oracle.image(v, cfg.pos_m, cfg.freq_hz, 2, 32, K, 1.0, gcf_kind=oracle.GCF_TABLE, oversample=os_,
+                       table=tab)
+    with E.Plan(cfg.pos_m, cfg.freq_hz, 2, 32, K, path=path, max_time=6, gcf_table=tab, oversample=os_) as plan:
+        got = plan.image(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert_parity(got, ref, path, "table gcf")
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_tiny_workload_full(path):
+    cfg = synth.config(1)
+    v = synth.make_voltages(cfg)
+    got = run_gpu(cfg, v, path)
+    assert_parity(got, oracle_image(cfg, v), path, "64-element 32x32 workload")
+    for c in range(cfg.n_chan):                         # the injected source is where Eq. 1 puts it
+        iy, ix = np.unravel_index(np.argmax(got[c, 0]), got.shape[2:])
+        assert ix in (19, 20) and iy in (14, 15)
+
+
+_BIG = {}
+
+
+def _big(idx):
+    if idx not in _BIG:
+        cfg = synth.config(idx)
+        _BIG[idx] = (cfg, synth.make_voltages(cfg))
+    return _BIG[idx]
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+@pytest.mark.parametrize("idx", [2, 3, 4])
+def test_full_workloads_sampled_channels(path, idx):
+    cfg, v = _big(idx)
+    got = run_gpu(cfg, v, path)
+    chans = [0, cfg.n_chan // 2 + 1, cfg.n_chan - 1]
+    assert_parity(got[chans], oracle_image(cfg, v, chans=chans), path, cfg.name)
+    assert np.all(np.isfinite(got))
+    # XX and YY are sums of squares everywhere
+    assert got[:, :2].min() >= -TOL[path] * got[:, :2].max()
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_accumulate_zero_length_and_split_blocks(path):
+    cfg = synth.small_config(n_ant=20, n_chan=3, n_pol=2, grid_n=32, gcf_k=3, n_time=13, seed=23)
+    v = synth.make_voltages(cfg)
+    ref = oracle_image(cfg, v)
+    with E.Plan.from_config(cfg, path=path) as plan:
+        d = torch.from_numpy(v).cuda()
+        out = torch.full((3, 4, 32, 32), 123.0, device="cuda")
+        plan.image(d[:0], out=out)                      # T = 0, reset: zero images
+        torch.cuda.synchronize()
+        assert float(out.abs().max()) == 0.0
+        plan.image(d[:5], out=out)
+        plan.image(d[5:5], out=out, accumulate=True)    # T = 0, accumulate: unchanged
+        plan.image(d[5:], out=out, accumulate=True)
+        assert_parity(out.cpu().numpy(), ref, path, "split block")
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_deterministic_and_host_call_identical(path):
+    cfg = synth.small_config(n_ant=48, n_chan=2, n_pol=2, grid_n=64, gcf_k=3, n_time=10, seed=31)
+    v = synth.make_voltages(cfg)
+    with E.Plan.from_config(cfg, path=path) as plan:
+        d = torch.from_numpy(v).cuda()
+        a = plan.image(d).cpu().numpy()
+        b = plan.image(d).cpu().numpy()
+        h = plan.image_host(v)
+        h2 = plan.image_host(v, out=h.copy(), accumulate=True)
+    assert np.array_equal(a, b)                         # no atomics: bitwise reruns
+    assert np.array_equal(a, h)
+    assert np.allclose(h2, 2 * a, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_invalid_calls_fail_before_launch(path):
+    cfg = synth.small_config(n_ant=10, n_chan=1, n_pol=2, grid_n=16, gcf_k=3, n_time=4, seed=1, diameter_m=5.0)
+    v = synth.make_voltages(cfg)
+    with E.Plan.from_config(cfg, path=path, max_time=4) as plan:
+        L = E.load()
+        out = torch.zeros((1, 4, 16, 16), device="cuda")
+        d = torch.from_numpy(v).cuda()
+        assert L.epic_image(plan._h, d.data_ptr(), 5, None, out.data_ptr(), 0) == 1       # T > max_time
+        assert L.epic_image(plan._h, d.data_ptr(), -1, None, out.data_ptr(), 0) == 1
+        assert L.epic_image(plan._h, v.ctypes.data, 4, None, out.data_ptr(), 0) == 1      # host pointer
+        assert L.epic_image(plan._h, d.data_ptr(), 4, None, out.data_ptr(), 8) == 1       # unknown flag
+        plan.sync()
