@@ -47,6 +47,11 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->dt.first_xy);
     cudaFree(p->dt.w_taps);
     cudaFree(p->dt.dft_f16);
+    cudaFree(p->tc.a1);
+    cudaFree(p->tc.a2);
+    cudaFree(p->tc.a1_off);
+    cudaFree(p->tc.a2_off);
+    cudaFree(p->tc.status);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);
     cudaFree(p->stage_out);
@@ -406,6 +411,16 @@ epic_status epic_sync(epic_plan_t p)
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return epic::cuda_fail(p, e, "epic_sync");
+    if (p->tc.status) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, p->tc.status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return epic::cuda_fail(p, e, "epic_sync(status)");
+        if (flag) {
+            cudaMemset(p->tc.status, 0, sizeof(int));
+            p->last_error = "a device-side bounded wait ran out; the images of that call are incomplete";
+            return EPIC_ERR_TIMEOUT;
+        }
+    }
     return EPIC_OK;
 }
 

@@ -31,6 +31,20 @@ struct DeviceTables {
     size_t dft_bytes = 0;
 };
 
+// Tensor-core path state (k_dftgemm.cu).
+struct TcState {
+    uint16_t* a1 = nullptr;        // stage-1 DFT operands per (channel, 64-column kx pair), FP16
+    uint16_t* a2 = nullptr;        // stage-2 DFT operands per (channel, 128-row ky block), FP16
+    long long* a1_off = nullptr;   // element offsets into a1 / a2
+    long long* a2_off = nullptr;
+    int* status = nullptr;         // device flag: 1 = a bounded wait ran out
+    int smem = 0;
+    unsigned sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0;
+    int n_g = 0, n_kb = 0, n_s = 0;
+    int cg = 0, tc = 0;            // channels per group, time samples per chunk
+    size_t stride = 0;             // bytes per grid tile in the chunk buffer
+};
+
 struct KernelEvent {
     const char* name;
     cudaEvent_t start, stop;
@@ -65,6 +79,7 @@ struct epic_plan_s {
     size_t stage_bytes = 0;
     int sm_count = 0;
     int smem_optin = 0;
+    epic::TcState tc;                     // tensor-core path
     int fused_variant = 0;                // kernel variant chosen for fused paths
     int slab = 0;                         // output columns per work item (fused paths)
 

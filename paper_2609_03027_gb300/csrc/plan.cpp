@@ -100,9 +100,15 @@ epic_status build_geometry(epic_plan_s* p, std::string* err)
                 }
             }
         }
-        p->box[c] = Box{xmin, ymin, xmax - xmin + 1, ymax - ymin + 1};
-        p->box_max_x = std::max(p->box_max_x, xmax - xmin + 1);
-        p->box_max_y = std::max(p->box_max_y, ymax - ymin + 1);
+        // Occupied box, widths padded (cells beyond the footprints stay empty): x to a
+        // multiple of 8, y to 8 (two pols) or 16 (one pol), as the tensor-core path needs
+        // (MMA K steps of 16 halves over re|im of x, N = pols x rows a multiple of 16).
+        const int padx = 8, pady = p->P == 2 ? 8 : 16;
+        const int nx = (xmax - xmin + 1 + padx - 1) / padx * padx;
+        const int ny = (ymax - ymin + 1 + pady - 1) / pady * pady;
+        p->box[c] = Box{xmin, ymin, nx, ny};
+        p->box_max_x = std::max(p->box_max_x, nx);
+        p->box_max_y = std::max(p->box_max_y, ny);
     }
     p->n_contrib = (size_t)C * A * K * K;
     return EPIC_OK;

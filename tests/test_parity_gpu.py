@@ -30,7 +30,7 @@ def run_gpu(cfg, volt, path, **kw):
     with E.Plan.from_config(cfg, path=path, max_time=max(1, volt.shape[0])) as plan:
         v = torch.from_numpy(volt).cuda()
         out = plan.image(v, **kw)
-        torch.cuda.synchronize()
+        plan.sync()                                     # also reports a device-side wait timeout
         return out.cpu().numpy()
 
 
