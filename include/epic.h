@@ -115,6 +115,9 @@ typedef struct {
     size_t device_bytes;    /* device memory owned by the plan                                    */
     size_t scratch_bytes;   /* part of device_bytes used as per-call scratch                      */
     int n_kernels;          /* kernels in one epic_image call for T = max_time                    */
+    double gemm_flops_per_sample; /* DFT-as-GEMM path: flops of the pruned two-stage transform per
+                                     time sample over all channels and pols (8 per complex MAC over
+                                     the occupied box); 0 for the FFT paths                        */
 } epic_plan_info;
 
 /* flags of epic_image / epic_image_host */

@@ -52,6 +52,8 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.a1_off);
     cudaFree(p->tc.a2_off);
     cudaFree(p->tc.status);
+    cudaFree(p->tc.a2w);
+    cudaFree(p->tc.a2w_off);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);
     cudaFree(p->stage_out);
@@ -311,8 +313,10 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
     int nk = 0;
     const int chunks = p->time_chunk > 0 ? (p->max_time + p->time_chunk - 1) / p->time_chunk : 1;
     if (p->path == EPIC_PATH_PLAIN_FP32) nk = 4 * chunks;
+    else if (p->path == EPIC_PATH_DFTGEMM_FP16) nk = 2 * chunks * ((p->C + p->tc.cg - 1) / std::max(1, p->tc.cg));
     else nk = p->scratch ? 2 : 1;
     info->n_kernels = nk;
+    info->gemm_flops_per_sample = p->path == EPIC_PATH_DFTGEMM_FP16 ? p->tc_flops_per_sample : 0.0;
     return EPIC_OK;
 }
 

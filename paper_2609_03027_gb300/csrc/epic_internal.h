@@ -43,6 +43,15 @@ struct TcState {
     int n_g = 0, n_kb = 0, n_s = 0;
     int cg = 0, tc = 0;            // channels per group, time samples per chunk
     size_t stride = 0;             // bytes per grid tile in the chunk buffer
+    unsigned b1_bytes = 0;         // bytes per shared-memory tile buffer
+    int nb = 1;                    // tile buffers (2 = next tile prefetched)
+    int grid_smem = 0;             // dynamic shared memory of the gridding kernel
+    bool grid_csr_smem = false;    // gridding kernel stages the cell lists in shared memory
+    bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2
+    uint32_t* a2w = nullptr;       // stage-2 operand rows as packed FP16 pairs (fast variant)
+    long long* a2w_off = nullptr;
+    unsigned b2_bytes = 0;
+    int d1_cols = 0;
 };
 
 struct KernelEvent {
@@ -67,6 +76,7 @@ struct epic_plan_s {
     std::vector<double> w_re, w_im;       // [C][A][K][K], conj(W) * (-1)^(jx+jy)
     int box_max_x = 0, box_max_y = 0;
     size_t n_contrib = 0;
+    double tc_flops_per_sample = 0.0;     // pruned DFT-as-GEMM flops per time sample (tensor path)
 
     // device state
     epic::DeviceTables dt;

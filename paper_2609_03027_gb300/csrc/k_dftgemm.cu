@@ -42,6 +42,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr size_t kScratchBudget = 96ull << 20;  // grid tiles of one (channel group, time chunk)
 constexpr long long kWaitBudget = 4000000000LL;  // clock cycles before a wait gives up (~2 s)
+constexpr int kGridFramesPerBlock = 8;            // frames gridded per block (cell lists read once)
 
 // ------------------------------------------------------------------ host helpers
 // IEEE binary16 bits of v, round to nearest even (written from the format definition).
@@ -68,8 +69,15 @@ uint16_t f16_bits(double v)
     return sign | (uint16_t)(E << 10) | (uint16_t)mant;
 }
 
-// element offset (in halves) of (row r, column k) in a [R][Kd] K-major core-matrix tile
-inline size_t core_off(int r, int k, int Kd) { return ((size_t)(r >> 3) * (Kd >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+// element offset (in halves) of (row r, column k) in an R-row operand stored in the
+// 128-byte swizzled K-major layout: 64-wide K panels of R rows x 128 bytes, the
+// 16-byte chunk c of row r at chunk position c ^ (r & 7).
+inline size_t sw_off(int r, int k, int R)
+{
+    return (size_t)(k >> 6) * ((size_t)R * 64) + (size_t)r * 64 + ((((k >> 3) & 7) ^ (r & 7)) << 3) + (k & 7);
+}
+
+__host__ __device__ inline int pad64(int k) { return (k + 63) & ~63; }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -87,6 +95,12 @@ struct MmaArgs {
     int accumulate;
     int* status;
     unsigned sA1, sA2, sB1, sB2;
+    unsigned b1_bytes;  // bytes per tile buffer in shared memory
+    // fast variant only
+    const uint32_t* a2w;        // stage-2 DFT operand rows as packed FP16 pairs, per (channel, ky block)
+    const long long* a2w_off;   // word offsets into a2w
+    unsigned b2_bytes;          // bytes per B2 buffer
+    int d1_cols;                // TMEM columns per D1 slot
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -95,17 +109,17 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b)
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ bool wait_uniform(uint64_t* bar, uint32_t parity)
+// byte offset of 16-byte chunk c (8 halves of K) of row r in an R-row operand in the
+// 128-byte swizzled K-major layout
+__device__ __forceinline__ size_t sw_chunk(int r, int c, int R)
 {
-    const bool ok = tc::mbar_wait(bar, parity, kWaitBudget);
-    return __syncthreads_and(ok) != 0;
+    return (size_t)(c >> 3) * ((size_t)R * 128) + (size_t)r * 128 + (((c & 7) ^ (r & 7)) << 4);
 }
 
-// Eight grid cells (x8*8 .. x8*8+7) of tile row R as two 16-byte core-matrix rows:
-// real parts at K chunk x8, imaginary parts at K chunk nxp/8 + x8.
-__device__ __forceinline__ void store_tile_row(uint8_t* tile, int R, int K1, int nxp, int x8, const float2 (&g)[8])
+// Eight grid cells (x8*8 .. x8*8+7) of tile row R (of N1 rows) as two 16-byte
+// chunks: real parts at K chunk x8, imaginary parts at K chunk nxp/8 + x8.
+__device__ __forceinline__ void store_tile_row(uint8_t* tile, int R, int N1, int nxp, int x8, const float2 (&g)[8])
 {
-    uint8_t* row = tile + ((size_t)(R >> 3) * (K1 >> 3)) * 128 + (R & 7) * 16;
     uint4 re, im;
     re.x = pack_h2(g[0].x, g[1].x);
     re.y = pack_h2(g[2].x, g[3].x);
@@ -115,8 +129,8 @@ __device__ __forceinline__ void store_tile_row(uint8_t* tile, int R, int K1, int
     im.y = pack_h2(g[2].y, g[3].y);
     im.z = pack_h2(g[4].y, g[5].y);
     im.w = pack_h2(g[6].y, g[7].y);
-    *reinterpret_cast<uint4*>(row + (size_t)x8 * 128) = re;
-    *reinterpret_cast<uint4*>(row + (size_t)((nxp >> 3) + x8) * 128) = im;
+    *reinterpret_cast<uint4*>(tile + sw_chunk(R, x8, N1)) = re;
+    *reinterpret_cast<uint4*>(tile + sw_chunk(R, (nxp >> 3) + x8, N1)) = im;
 }
 
 // 16 consecutive image pixels of one product: written, or added to what is there.
@@ -142,9 +156,13 @@ __device__ __forceinline__ void store_pixels16(float* op, int nk, int accumulate
     }
 }
 
-// Unpack and gather-grid the frames of one chunk into FP16 UMMA tiles.
+// Unpack and gather-grid frames of one chunk into FP16 UMMA tiles.  A block
+// handles `fpc` consecutive frames of one channel so that the channel's cell
+// lists are read once; with CSR_SMEM they are staged in shared memory as
+// (element, real weight) pairs (Gaussian GCF), otherwise read through L1.
+template <bool CSR_SMEM>
 __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __restrict__ volt, int t0, int c0,
-                                                           int n_ch, int C, int A, int P,
+                                                           int n_ch, int nt, int fpc, int C, int A, int P,
                                                            const int4* __restrict__ box,
                                                            const int* __restrict__ cell_off,
                                                            const int* __restrict__ cell_ptr,
@@ -152,34 +170,64 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                                                            const float2* __restrict__ cw, uint8_t* __restrict__ tiles,
                                                            unsigned long long tile_stride)
 {
-    extern __shared__ float2 sv[];  // [A][P]
-    const int tl = blockIdx.x, cl = blockIdx.y, c = c0 + cl;
-    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
-    for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = unpack44(fr[i]);
-    __syncthreads();
+    extern __shared__ __align__(16) uint8_t gsm[];
+    float2* sv = reinterpret_cast<float2*>(gsm);  // [A][P]
+    const int cl = blockIdx.y, c = c0 + cl;
     const int4 b = box[c];
-    const int nxp = b.z, nyp = b.w, K1 = 2 * nxp;
-    const int* ptr = cell_ptr + cell_off[c];
-    uint8_t* tile = tiles + ((size_t)tl * n_ch + cl) * tile_stride;
+    const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
+    const int* gptr = cell_ptr + cell_off[c];
+    const int* ptr = gptr;
+    int2* con = nullptr;
+    int base = 0;
+    if (CSR_SMEM) {
+        int* sptr = reinterpret_cast<int*>(gsm + sizeof(float2) * (size_t)A * P);
+        con = reinterpret_cast<int2*>(sptr + ((ncell + 2) & ~1));
+        base = gptr[0];
+        const int ncon = gptr[ncell] - base;
+        for (int i = threadIdx.x; i <= ncell; i += blockDim.x) sptr[i] = gptr[i] - base;
+        for (int i = threadIdx.x; i < ncon; i += blockDim.x) con[i] = make_int2(ce[base + i], __float_as_int(cw[base + i].x));
+        ptr = sptr;
+    }
+    const int f0 = blockIdx.x * fpc, f1 = min(nt, f0 + fpc);
     const int tasks = nyp * (nxp >> 3);
-    for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
-        const int y = task % nyp, x8 = task / nyp;
-        const int r0 = y * nxp + x8 * 8;
-        float2 gx[8], gy[8];
+    for (int tl = f0; tl < f1; ++tl) {
+        __syncthreads();
+        const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
+        for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = unpack44(fr[i]);
+        __syncthreads();
+        uint8_t* tile = tiles + ((size_t)tl * n_ch + cl) * tile_stride;
+        for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
+            const int y = task % nyp, x8 = task / nyp;
+            const int r0 = y * nxp + x8 * 8;
+            float2 gx[8], gy[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            gx[i] = make_float2(0.f, 0.f);
-            gy[i] = make_float2(0.f, 0.f);
-            const int q1 = ptr[r0 + i + 1];
-            for (int q = ptr[r0 + i]; q < q1; ++q) {
-                const int e = ce[q];
-                const float2 w = cw[q];
-                gx[i] = cfma(w, sv[e * P], gx[i]);
-                if (P == 2) gy[i] = cfma(w, sv[e * P + 1], gy[i]);
+            for (int i = 0; i < 8; ++i) {
+                gx[i] = make_float2(0.f, 0.f);
+                gy[i] = make_float2(0.f, 0.f);
+                const int q1 = ptr[r0 + i + 1];
+                for (int q = ptr[r0 + i]; q < q1; ++q) {
+                    if (CSR_SMEM) {
+                        const int2 cr = con[q];
+                        const float w = __int_as_float(cr.y);
+                        const float2 vx = sv[cr.x * P];
+                        gx[i].x = fmaf(w, vx.x, gx[i].x);
+                        gx[i].y = fmaf(w, vx.y, gx[i].y);
+                        if (P == 2) {
+                            const float2 vy = sv[cr.x * P + 1];
+                            gy[i].x = fmaf(w, vy.x, gy[i].x);
+                            gy[i].y = fmaf(w, vy.y, gy[i].y);
+                        }
+                    } else {
+                        const int e = ce[q];
+                        const float2 w = cw[q];
+                        gx[i] = cfma(w, sv[e * P], gx[i]);
+                        if (P == 2) gy[i] = cfma(w, sv[e * P + 1], gy[i]);
+                    }
+                }
             }
+            store_tile_row(tile, 0 * nyp + y, N1, nxp, x8, gx);
+            if (P == 2) store_tile_row(tile, 1 * nyp + y, N1, nxp, x8, gy);
         }
-        store_tile_row(tile, 0 * nyp + y, K1, nxp, x8, gx);
-        if (P == 2) store_tile_row(tile, 1 * nyp + y, K1, nxp, x8, gy);
     }
 }
 
@@ -191,35 +239,198 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r)
                  : "memory");
 }
 
+__device__ __forceinline__ bool wait_flag_uniform(uint64_t* bar, uint32_t parity, const volatile int* err)
+{
+    const bool ok = tc::mbar_wait(bar, parity, kWaitBudget);
+    return __syncthreads_and(ok && *err == 0) != 0;
+}
+
+// Epilogue 2: products of the stage-2 result in TMEM columns col0.. (pol X at
+// col0, pol Y at col0 + 64; re at +0, im at +32) added to the accumulators.
+__device__ __forceinline__ void epilogue2(uint32_t taddr, int P, float (&axx)[16], float (&ayy)[16], float (&arx)[16],
+                                          float (&aix)[16])
+{
+    uint32_t xr[16], xi[16];
+    tc::tmem_ld16(taddr, xr);
+    tc::tmem_ld16(taddr + 32, xi);
+    if (P == 2) {
+        uint32_t yr[16], yi[16];
+        tc::tmem_ld16(taddr + 64, yr);
+        tc::tmem_ld16(taddr + 96, yi);
+        tc::tmem_wait_ld(xr);
+        tc::tmem_wait_ld(xi);
+        tc::tmem_wait_ld(yr);
+        tc::tmem_wait_ld(yi);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float Xr = __uint_as_float(xr[i]), Xi = __uint_as_float(xi[i]);
+            const float Yr = __uint_as_float(yr[i]), Yi = __uint_as_float(yi[i]);
+            axx[i] = fmaf(Xr, Xr, fmaf(Xi, Xi, axx[i]));
+            ayy[i] = fmaf(Yr, Yr, fmaf(Yi, Yi, ayy[i]));
+            arx[i] = fmaf(Xr, Yr, fmaf(Xi, Yi, arx[i]));
+            aix[i] = fmaf(Xi, Yr, fmaf(-Xr, Yi, aix[i]));
+        }
+    } else {
+        tc::tmem_wait_ld(xr);
+        tc::tmem_wait_ld(xi);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float Xr = __uint_as_float(xr[i]), Xi = __uint_as_float(xi[i]);
+            axx[i] = fmaf(Xr, Xr, fmaf(Xi, Xi, axx[i]));
+        }
+    }
+}
+
+// Epilogue 1 of one pol: the stage-1 result of this warp's lane quarter (lanes =
+// the slab's 32 kx; quarter 0 holds Hr, quarter 1 Hi) for the pol's nyp columns,
+// converted to FP16 and written as the stage-2 operand B2_p:
+//   row kx      = [ Hr[0..nyp) | -Hi[0..nyp) ],  row 32+kx = [ Hi | Hr ].
+// TMEM loads are issued 32 columns at a time before one wait.
+__device__ __forceinline__ void epilogue1(uint32_t taddr, int nyp, bool imw, int lane, uint8_t* b2, int p, int R2)
+{
+    const int n0 = 64 * p + lane, n1 = 64 * p + 32 + lane;
+    for (int y0 = 0; y0 < nyp; y0 += 32) {
+        const int ng = min(4, (nyp - y0) >> 3);  // groups of 8 columns in this batch
+        uint32_t r[32];
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (g < ng) tmem_ld8(taddr + y0 + 8 * g, r + 8 * g);
+        tc::tmem_wait_ld(r);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            if (g >= ng) break;
+            uint4 pos, neg;
+            pos.x = pack_h2(__uint_as_float(r[8 * g + 0]), __uint_as_float(r[8 * g + 1]));
+            pos.y = pack_h2(__uint_as_float(r[8 * g + 2]), __uint_as_float(r[8 * g + 3]));
+            pos.z = pack_h2(__uint_as_float(r[8 * g + 4]), __uint_as_float(r[8 * g + 5]));
+            pos.w = pack_h2(__uint_as_float(r[8 * g + 6]), __uint_as_float(r[8 * g + 7]));
+            neg.x = pos.x ^ 0x80008000u;  // FP16 negation = sign-bit flip
+            neg.y = pos.y ^ 0x80008000u;
+            neg.z = pos.z ^ 0x80008000u;
+            neg.w = pos.w ^ 0x80008000u;
+            const int kc_lo = (y0 >> 3) + g, kc_hi = (nyp >> 3) + kc_lo;
+            if (!imw) {  // Hr: B2[kx][y] and B2[32+kx][nyp+y]
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_lo, R2)) = pos;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_hi, R2)) = pos;
+            } else {     // Hi: B2[kx][nyp+y] = -Hi, B2[32+kx][y] = Hi
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_hi, R2)) = neg;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_lo, R2)) = pos;
+            }
+        }
+    }
+}
+
+// MMA chains over KS K steps accumulating into one TMEM tile.  Descriptors are
+// derived from a base by adding, in 16-byte units, (k / 4) * panel + (k % 4) * 2
+// (a 64-wide K panel of the swizzled layout, then 32 bytes per K step inside it);
+// the loops are unrolled at compile time so that issuing costs no more than the
+// tensor core's own time per MMA.
+template <int KS>
+__device__ __forceinline__ void chain_ss(uint32_t d, uint64_t da, uint64_t db, uint32_t pa16, uint32_t pb16,
+                                         uint32_t id)
+{
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+        tc::mma_f16(d, da + (uint64_t)((k >> 2) * pa16 + (k & 3) * 2), db + (uint64_t)((k >> 2) * pb16 + (k & 3) * 2),
+                    id, k > 0);
+}
+
+template <int KS>
+__device__ __forceinline__ void chain_ts(uint32_t d, uint32_t at, uint64_t db, uint32_t pb16, uint32_t id)
+{
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+        tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb16 + (k & 3) * 2), id, k > 0);
+}
+
+#define EPIC_KS_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+// A and B in shared memory (both 128-byte swizzled, K-major)
+__device__ __forceinline__ void issue_ss(int ks, uint32_t d, uint32_t sa, uint32_t sb, uint32_t a_panel_bytes,
+                                         uint32_t b_panel_bytes, uint32_t id)
+{
+    const uint64_t da = tc::smem_desc_sw128(sa), db = tc::smem_desc_sw128(sb);
+    const uint32_t pa = a_panel_bytes >> 4, pb = b_panel_bytes >> 4;
+    switch (ks) {
+#define EPIC_SS(n) \
+    case n: chain_ss<n>(d, da, db, pa, pb, id); break;
+        EPIC_KS_CASES(EPIC_SS)
+#undef EPIC_SS
+        default:
+            for (int k = 0; k < ks; ++k)
+                tc::mma_f16(d, da + (uint64_t)((k >> 2) * pa + (k & 3) * 2), db + (uint64_t)((k >> 2) * pb + (k & 3) * 2),
+                            id, k > 0);
+    }
+}
+
+// A in TMEM (K halves packed in pairs: 8 columns per K step), B in shared memory
+__device__ __forceinline__ void issue_ts(int ks, uint32_t d, uint32_t at, uint32_t sb, uint32_t b_panel_bytes,
+                                         uint32_t id)
+{
+    const uint64_t db = tc::smem_desc_sw128(sb);
+    const uint32_t pb = b_panel_bytes >> 4;
+    switch (ks) {
+#define EPIC_TS(n) \
+    case n: chain_ts<n>(d, at, db, pb, id); break;
+        EPIC_KS_CASES(EPIC_TS)
+#undef EPIC_TS
+        default:
+            for (int k = 0; k < ks; ++k)
+                tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb + (k & 3) * 2), id, k > 0);
+    }
+}
+
 // Stage 1 + stage 2 + products + accumulation for the work items of one chunk.
-__global__ void __launch_bounds__(kThreads, 1) k_dftgemm_mma(MmaArgs a)
+// Warps 0-7 do the epilogues; lane 0 of warp 3 (which has no epilogue-1 work)
+// also drives the TMA engine and the tensor core.  The frame loop is
+// software-pipelined:
+//   all wait until S2(t-1) and S1(t) are complete
+//   control: refill the tile buffer S1(t) released with tile t+NB
+//   warps 0,1 (pol X) and 4,5 (pol Y): epilogue 1 (t): D1 -> FP16 B2     | barrier
+//   control: issue S2(t) into D2[t&1], then S1(t+1) into D1, commit
+//   warps 0-7: epilogue 2 (t-1) from D2[(t-1)&1] while the tensor core runs
+// TMEM: D1 in columns [0, 256), D2[b] in [256 + 128 b, 384 + 128 b).
+// A1 rows 0..31 = re, 32..63 = im of the item's own 32 kx (rows 64..127 zero),
+// so epilogue 1 reads lane quarters 0 (Hr) and 1 (Hi).
+constexpr int kMmaThreads = 256;
+
+template <int NB>
+__global__ void __launch_bounds__(kMmaThreads, 1) k_dftgemm_mma(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bar_mma, bar_tma;
+    __shared__ uint64_t bar_mma, bar_a, bar_tile[2];
     __shared__ uint32_t tmem_sh;
+    __shared__ int err_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctl = tid == 3 * 32;  // the control thread (warp 3, lane 0)
     if (warp == 0) {
         tc::tmem_alloc(&tmem_sh, 512);
         tc::tmem_relinquish();
     }
-    if (tid == 0) {
+    if (ctl) {
         tc::mbar_init(&bar_mma, 1);
-        tc::mbar_init(&bar_tma, 1);
+        tc::mbar_init(&bar_a, 1);
+        tc::mbar_init(&bar_tile[0], 1);
+        tc::mbar_init(&bar_tile[1], 1);
+        err_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_sh;
-    uint8_t* sA1 = smem + a.sA1;
-    uint8_t* sA2 = smem + a.sA2;
-    uint8_t* sB1 = smem + a.sB1;
-    uint8_t* sB2 = smem + a.sB2;
-    uint32_t ph_mma = 0, ph_tma = 0;
+    // swizzled operands need 1024-byte aligned bases (the swizzle uses address bits 4-9)
+    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+    uint8_t* sA1 = sbase + a.sA1;
+    uint8_t* sA2 = sbase + a.sA2;
+    uint8_t* sB2 = sbase + a.sB2;
+    uint32_t ph_mma = 0, ph_a = 0;
+    uint32_t ph_tile = 0;  // bit b = parity of tile buffer b (control thread only)
     bool ok = true;
     const int items = a.n_ch * a.n_kb * a.n_s;
     const int q4 = warp & 3, hc = warp >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+    const bool epi1 = q4 < 2 && (warp >> 2) < a.P;  // warps 0, 1 (pol 0) and 4, 5 (pol 1)
 
     for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
         const int s = item % a.n_s, kb = (item / a.n_s) % a.n_kb, cl = item / (a.n_s * a.n_kb);
@@ -227,131 +438,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_dftgemm_mma(MmaArgs a)
         const int4 bx = a.box[c];
         const int nxp = bx.z, nyp = bx.w;
         const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = a.P * nyp;
-        const int g = s >> 1, h = s & 1;
-        const uint32_t a1_bytes = 256u * K1, a2_bytes = 256u * K2;
-        const uint32_t tile_bytes = (uint32_t)N1 * K1 * 2;
-        if (tid == 0) {
-            tc::mbar_expect_tx(&bar_tma, a1_bytes + a2_bytes);
-            tc::bulk_g2s(sA1, a.a1 + a.a1_off[(size_t)c * a.n_g + g], a1_bytes, &bar_tma);
-            tc::bulk_g2s(sA2, a.a2 + a.a2_off[(size_t)c * a.n_kb + kb], a2_bytes, &bar_tma);
+        const int K1s = pad64(K1), K2s = pad64(K2);
+        const uint32_t a1_bytes = 256u * K1s, a2_bytes = 256u * K2s;
+        const uint32_t tile_bytes = (uint32_t)N1 * K1s * 2;
+        const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
+        const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+        const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 64 * a.P);
+        const int nt = a.nt;
+
+        auto issue_s1 = [&](int b) {
+            issue_ss(K1 / 16, tmem, tc::smem_u32(sA1), tc::smem_u32(sbase + a.sB1 + (size_t)b * a.b1_bytes), 128 * 128,
+                     N1 * 128, id1);
+        };
+        auto issue_s2 = [&](int d) {  // both pols in one MMA: B2 rows 0..63 pol X, 64..127 pol Y
+            issue_ss(K2 / 16, tmem + 256 + 128 * d, tc::smem_u32(sA2), tc::smem_u32(sB2), 128 * 128, 64 * a.P * 128,
+                     id2);
+        };
+        auto load_tile = [&](int t, int b) {
+            tc::mbar_expect_tx(&bar_tile[b], tile_bytes);
+            tc::bulk_g2s(sbase + a.sB1 + (size_t)b * a.b1_bytes, tiles_c + (size_t)t * frame_step, tile_bytes,
+                         &bar_tile[b]);
+        };
+        auto wait_tile = [&](int b) -> bool {
+            const bool r = tc::mbar_wait(&bar_tile[b], (ph_tile >> b) & 1u, kWaitBudget);
+            ph_tile ^= 1u << b;
+            if (!r) err_sh = 1;
+            return r;
+        };
+
+        if (ctl) {
+            tc::mbar_expect_tx(&bar_a, a1_bytes + a2_bytes);
+            tc::bulk_g2s(sA1, a.a1 + a.a1_off[(size_t)c * a.n_s + s], a1_bytes, &bar_a);
+            tc::bulk_g2s(sA2, a.a2 + a.a2_off[(size_t)c * a.n_kb + kb], a2_bytes, &bar_a);
+            for (int j = 0; j < NB && j < nt; ++j) load_tile(j, j);
         }
-        ok = wait_uniform(&bar_tma, ph_tma);
-        ph_tma ^= 1;
+        ok = wait_flag_uniform(&bar_a, ph_a, &err_sh);
+        ph_a ^= 1;
+        if (!ok) break;
+        if (ctl) {
+            if (wait_tile(0)) {
+                tc::fence_after_sync();
+                issue_s1(0);
+            }
+            tc::mma_commit(&bar_mma);
+        }
 
         float axx[16], ayy[16], arx[16], aix[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
 
-        const uint32_t sbo1 = (uint32_t)(K1 / 8) * 128, sbo2 = (uint32_t)(K2 / 8) * 128;
-        for (int t = 0; ok && t < a.nt; ++t) {
-            // ---- grid tile of (t, c) -> shared memory
-            if (tid == 0) {
-                tc::mbar_expect_tx(&bar_tma, tile_bytes);
-                tc::bulk_g2s(sB1, a.tiles + ((size_t)t * a.n_ch + cl) * a.tile_stride, tile_bytes, &bar_tma);
-            }
-            ok = wait_uniform(&bar_tma, ph_tma);
-            ph_tma ^= 1;
-            if (!ok) break;
-            // ---- stage 1: D1 = A1 . B1^T  (M = 128, N = N1, K = K1)
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t ia = tc::smem_u32(sA1), ib = tc::smem_u32(sB1);
-                const uint32_t id1 = tc::idesc_f16_f32(128, N1);
-                for (int k = 0; k < K1 / 16; ++k)
-                    tc::mma_f16(tmem, tc::smem_desc(ia + k * 256, 128, sbo1), tc::smem_desc(ib + k * 256, 128, sbo1),
-                                id1, k > 0);
-                tc::mma_commit(&bar_mma);
-            }
-            ok = wait_uniform(&bar_mma, ph_mma);
+        for (int t = 0; ok && t < nt; ++t) {
+            ok = wait_flag_uniform(&bar_mma, ph_mma, &err_sh);  // S2(t-1) and S1(t) complete
             ph_mma ^= 1;
             if (!ok) break;
             tc::fence_after_sync();
-            // ---- epilogue 1: H of this slab (lanes 32h.. re, 64+32h.. im) -> FP16 B2_p
-            if (warp == h || warp == 2 + h) {
-                const bool imw = warp >= 2;
-                for (int p = 0; p < a.P; ++p) {
-                    uint8_t* b2 = sB2 + (size_t)p * 64 * K2 * 2;
-                    for (int yc = 0; yc < nyp / 8; ++yc) {
-                        uint32_t r[8];
-                        tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + p * nyp + yc * 8, r);
-                        tc::tmem_wait_ld(r);
-                        float v[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-                        uint4 pos, neg;
-                        pos.x = pack_h2(v[0], v[1]);
-                        pos.y = pack_h2(v[2], v[3]);
-                        pos.z = pack_h2(v[4], v[5]);
-                        pos.w = pack_h2(v[6], v[7]);
-                        neg.x = pack_h2(-v[0], -v[1]);
-                        neg.y = pack_h2(-v[2], -v[3]);
-                        neg.z = pack_h2(-v[4], -v[5]);
-                        neg.w = pack_h2(-v[6], -v[7]);
-                        const int n0 = lane, n1 = 32 + lane;
-                        uint8_t* row0 = b2 + ((size_t)(n0 >> 3) * (K2 >> 3)) * 128 + (n0 & 7) * 16;
-                        uint8_t* row1 = b2 + ((size_t)(n1 >> 3) * (K2 >> 3)) * 128 + (n1 & 7) * 16;
-                        const int kc_lo = yc, kc_hi = (nyp >> 3) + yc;
-                        if (!imw) {  // Hr: B2[kx][y] and B2[32+kx][nyp+y]
-                            *reinterpret_cast<uint4*>(row0 + (size_t)kc_lo * 128) = pos;
-                            *reinterpret_cast<uint4*>(row1 + (size_t)kc_hi * 128) = pos;
-                        } else {     // Hi: B2[kx][nyp+y] = -Hi, B2[32+kx][y] = Hi
-                            *reinterpret_cast<uint4*>(row0 + (size_t)kc_hi * 128) = neg;
-                            *reinterpret_cast<uint4*>(row1 + (size_t)kc_lo * 128) = pos;
-                        }
-                    }
-                }
+            if (ctl && t + NB < nt) load_tile(t + NB, t % NB);  // S1(t) has released that buffer
+            if (epi1) {
+                const int p = warp >> 2;
+                epilogue1(tmem + ((uint32_t)(32 * q4) << 16) + p * nyp, nyp, q4 == 1, lane, sB2, p, 64 * a.P);
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
-            // ---- stage 2: D2_p = A2 . B2_p^T  (M = 128, N = 64, K = K2), TMEM columns 256 + 64 p
-            if (tid == 0) {
-                const uint32_t ia = tc::smem_u32(sA2);
-                const uint32_t id2 = tc::idesc_f16_f32(128, 64);
-                for (int p = 0; p < a.P; ++p) {
-                    const uint32_t ib = tc::smem_u32(sB2) + (uint32_t)p * 64 * K2 * 2;
-                    for (int k = 0; k < K2 / 16; ++k)
-                        tc::mma_f16(tmem + 256 + 64 * p, tc::smem_desc(ia + k * 256, 128, sbo2),
-                                    tc::smem_desc(ib + k * 256, 128, sbo2), id2, k > 0);
+            if (ctl) {
+                issue_s2(t & 1);
+                if (t + 1 < nt && wait_tile((t + 1) % NB)) {
+                    tc::fence_after_sync();
+                    issue_s1((t + 1) % NB);
                 }
                 tc::mma_commit(&bar_mma);
             }
-            ok = wait_uniform(&bar_mma, ph_mma);
+            __syncwarp();
+            if (t >= 1)
+                epilogue2(tmem + lane_base + 256 + 128 * ((t - 1) & 1) + 16 * hc, a.P, axx, ayy, arx, aix);
+            tc::fence_before_sync();
+        }
+        if (ok && nt > 0) {
+            ok = wait_flag_uniform(&bar_mma, ph_mma, &err_sh);  // S2(nt-1)
             ph_mma ^= 1;
-            if (!ok) break;
-            tc::fence_after_sync();
-            // ---- epilogue 2: products and accumulation (row ky = 32 q4 + lane, 16 kx per thread)
-            {
-                uint32_t xr[16], xi[16];
-                tc::tmem_ld16(tmem + lane_base + 256 + 16 * hc, xr);
-                tc::tmem_ld16(tmem + lane_base + 256 + 32 + 16 * hc, xi);
-                if (a.P == 2) {
-                    uint32_t yr[16], yi[16];
-                    tc::tmem_ld16(tmem + lane_base + 256 + 64 + 16 * hc, yr);
-                    tc::tmem_ld16(tmem + lane_base + 256 + 96 + 16 * hc, yi);
-                    tc::tmem_wait_ld(xr);
-                    tc::tmem_wait_ld(xi);
-                    tc::tmem_wait_ld(yr);
-                    tc::tmem_wait_ld(yi);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float Xr = __uint_as_float(xr[i]), Xi = __uint_as_float(xi[i]);
-                        const float Yr = __uint_as_float(yr[i]), Yi = __uint_as_float(yi[i]);
-                        axx[i] = fmaf(Xr, Xr, fmaf(Xi, Xi, axx[i]));
-                        ayy[i] = fmaf(Yr, Yr, fmaf(Yi, Yi, ayy[i]));
-                        arx[i] = fmaf(Xr, Yr, fmaf(Xi, Yi, arx[i]));
-                        aix[i] = fmaf(Xi, Yr, fmaf(-Xr, Yi, aix[i]));
-                    }
-                } else {
-                    tc::tmem_wait_ld(xr);
-                    tc::tmem_wait_ld(xi);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float Xr = __uint_as_float(xr[i]), Xi = __uint_as_float(xi[i]);
-                        axx[i] = fmaf(Xr, Xr, fmaf(Xi, Xi, axx[i]));
-                    }
-                }
+            if (ok) {
+                tc::fence_after_sync();
+                epilogue2(tmem + lane_base + 256 + 128 * ((nt - 1) & 1) + 16 * hc, a.P, axx, ayy, arx, aix);
             }
             tc::fence_before_sync();
             __syncthreads();
@@ -376,7 +544,205 @@ __global__ void __launch_bounds__(kThreads, 1) k_dftgemm_mma(MmaArgs a)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
-    if (!ok && tid == 0) atomicExch(a.status, 1);
+    if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
+}
+
+// Fast variant for occupied boxes small enough that two stage-1 results, the
+// stage-2 DFT operand and two stage-2 results all fit in TMEM (2 N1 + K2/2 <= 256
+// columns) and three grid tiles plus two B2 buffers fit in shared memory.
+//   TMEM: D1[b] at b*d1_cols, A2 (FP16 pairs) at 2*d1_cols, D2[b] at 256 + 128 b.
+//   The stage-2 A operand (the constant ky DFT rows) is read from TMEM, so stage 2
+//   streams only B2 from shared memory.
+// Schedule (tensor order S1(0) S1(1) S2(0) S1(2) S2(1) S1(3) ...):
+//   iteration t: wait S1(t) -> control refills tile t+3 -> epilogue 1 (t): D1[t&1] ->
+//   B2[t&1] | barrier | control issues S2(t) -> D2[t&1] (commit s2[t&1]) and
+//   S1(t+2) -> D1[t&1] (commit s1[t&1]) | epilogue 2 (t-1) after S2(t-1).
+// While the warps convert frame t the tensor core runs S1(t+1) and S2(t-1).
+template <int dummy>
+__global__ void __launch_bounds__(kMmaThreads, 1) k_dftgemm_mma_fast(MmaArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar_a, bar_s1[2], bar_s2[2], bar_tile[3];
+    __shared__ uint32_t tmem_sh;
+    __shared__ int err_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctl = tid == 3 * 32;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_sh, 512);
+        tc::tmem_relinquish();
+    }
+    if (ctl) {
+        tc::mbar_init(&bar_a, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&bar_s1[i], 1);
+            tc::mbar_init(&bar_s2[i], 1);
+        }
+        for (int i = 0; i < 3; ++i) tc::mbar_init(&bar_tile[i], 1);
+        err_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_sh;
+    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+    uint8_t* sA1 = sbase + a.sA1;
+    uint32_t ph_a = 0, ph_s1 = 0, ph_s2 = 0;  // bit b: parity of slot b
+    uint32_t ph_tile = 0;                     // control thread: bit b parity of tile buffer b
+    bool ok = true;
+    const int items = a.n_ch * a.n_kb * a.n_s;
+    const int q4 = warp & 3, hc = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+    const bool epi1 = q4 < 2 && (warp >> 2) < a.P;
+    const uint32_t a2col = 2u * a.d1_cols;
+
+    for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
+        const int s = item % a.n_s, kb = (item / a.n_s) % a.n_kb, cl = item / (a.n_s * a.n_kb);
+        const int c = a.c0 + cl;
+        const int4 bx = a.box[c];
+        const int nxp = bx.z, nyp = bx.w;
+        const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = a.P * nyp;
+        const int K1s = pad64(K1);
+        const uint32_t a1_bytes = 256u * K1s;
+        const uint32_t tile_bytes = (uint32_t)N1 * K1s * 2;
+        const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
+        const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+        const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 64 * a.P);
+        const int nt = a.nt;
+        const int R2 = 64 * a.P;
+
+        auto issue_s1 = [&](int b, int slot) {
+            issue_ss(K1 / 16, tmem + slot * a.d1_cols, tc::smem_u32(sA1),
+                     tc::smem_u32(sbase + a.sB1 + (size_t)b * a.b1_bytes), 128 * 128, N1 * 128, id1);
+        };
+        auto issue_s2 = [&](int slot) {
+            issue_ts(K2 / 16, tmem + 256 + 128 * slot, tmem + a2col,
+                     tc::smem_u32(sbase + a.sB2 + (size_t)slot * a.b2_bytes), R2 * 128, id2);
+        };
+        auto load_tile = [&](int t) {
+            const int b = t % 3;
+            tc::mbar_expect_tx(&bar_tile[b], tile_bytes);
+            tc::bulk_g2s(sbase + a.sB1 + (size_t)b * a.b1_bytes, tiles_c + (size_t)t * frame_step, tile_bytes,
+                         &bar_tile[b]);
+        };
+        auto wait_tile = [&](int t) -> bool {
+            const int b = t % 3;
+            const bool r = tc::mbar_wait(&bar_tile[b], (ph_tile >> b) & 1u, kWaitBudget);
+            ph_tile ^= 1u << b;
+            if (!r) err_sh = 1;
+            return r;
+        };
+        auto wait_slot = [&](uint64_t* bars, uint32_t& ph, int slot) -> bool {
+            const bool r = tc::mbar_wait(&bars[slot], (ph >> slot) & 1u, kWaitBudget);
+            ph ^= 1u << slot;
+            if (!r) err_sh = 1;
+            return r;
+        };
+
+        if (ctl) {
+            tc::mbar_expect_tx(&bar_a, a1_bytes);
+            tc::bulk_g2s(sA1, a.a1 + a.a1_off[(size_t)c * a.n_s + s], a1_bytes, &bar_a);
+            for (int j = 0; j < 3 && j < nt; ++j) load_tile(j);
+        }
+        __syncwarp();
+        // stage-2 DFT operand -> TMEM (warps 0-3: lane = ky row)
+        if (warp < 4) {
+            const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
+            for (int j = 0; j < K2 / 2; j += 8) {
+                uint32_t r[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r[i] = src[j + i];
+                tc::tmem_st8(tmem + lane_base + a2col + j, r);
+            }
+            tc::tmem_wait_st();
+        }
+        tc::fence_before_sync();
+        ok = wait_flag_uniform(&bar_a, (ph_a & 1u), &err_sh);
+        ph_a ^= 1;
+        if (!ok) break;
+        tc::fence_after_sync();
+        if (ctl) {
+            for (int j = 0; j < 2 && j < nt; ++j) {
+                if (wait_tile(j)) {
+                    tc::fence_after_sync();
+                    issue_s1(j % 3, j);
+                }
+                tc::mma_commit(&bar_s1[j]);
+            }
+        }
+
+        float axx[16], ayy[16], arx[16], aix[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+
+        for (int t = 0; ok && t < nt; ++t) {
+            const int sl = t & 1;
+            bool w = wait_slot(bar_s1, ph_s1, sl);           // S1(t) (and S2(t-2)) complete
+            ok = __syncthreads_and(w && err_sh == 0) != 0;
+            if (!ok) break;
+            tc::fence_after_sync();
+            if (ctl && t + 3 < nt) load_tile(t + 3);          // S1(t) released tile buffer t % 3
+            if (epi1) {
+                const int p = warp >> 2;
+                epilogue1(tmem + ((uint32_t)(32 * q4) << 16) + sl * a.d1_cols + p * nyp, nyp, q4 == 1, lane,
+                          sbase + a.sB2 + (size_t)sl * a.b2_bytes, p, R2);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (ctl) {
+                issue_s2(sl);
+                tc::mma_commit(&bar_s2[sl]);
+                if (t + 2 < nt) {
+                    if (wait_tile(t + 2)) {
+                        tc::fence_after_sync();
+                        issue_s1((t + 2) % 3, sl);
+                    }
+                    tc::mma_commit(&bar_s1[sl]);
+                }
+            }
+            __syncwarp();
+            if (t >= 1) {
+                const bool w2 = wait_slot(bar_s2, ph_s2, (t - 1) & 1);
+                __syncwarp();
+                if (w2) {
+                    tc::fence_after_sync();
+                    epilogue2(tmem + lane_base + 256 + 128 * ((t - 1) & 1) + 16 * hc, a.P, axx, ayy, arx, aix);
+                }
+            }
+            tc::fence_before_sync();
+        }
+        if (ok && nt > 0) {
+            const bool w = wait_slot(bar_s2, ph_s2, (nt - 1) & 1);
+            __syncwarp();
+            if (w) {
+                tc::fence_after_sync();
+                epilogue2(tmem + lane_base + 256 + 128 * ((nt - 1) & 1) + 16 * hc, a.P, axx, ayy, arx, aix);
+            }
+            tc::fence_before_sync();
+            ok = __syncthreads_and(w && err_sh == 0) != 0;
+            tc::fence_after_sync();
+        }
+        if (!ok) break;
+        const int ky = 128 * kb + 32 * q4 + lane;
+        const int kx0 = 32 * s + 16 * hc;
+        if (ky < a.N && kx0 < a.N) {
+            const size_t NN = (size_t)a.N * a.N;
+            float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
+            const int nk = min(16, a.N - kx0);
+            store_pixels16(o, nk, a.accumulate, axx);
+            if (a.nprod == 4) {
+                store_pixels16(o + NN, nk, a.accumulate, ayy);
+                store_pixels16(o + 2 * NN, nk, a.accumulate, arx);
+                store_pixels16(o + 3 * NN, nk, a.accumulate, aix);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
 }
 
 }  // namespace
@@ -384,47 +750,82 @@ __global__ void __launch_bounds__(kThreads, 1) k_dftgemm_mma(MmaArgs a)
 epic_status dftgemm_setup(epic_plan_s* p)
 {
     const int N = p->N, C = p->C, P = p->P;
-    const int n_g = (N + 63) / 64, n_kb = (N + 127) / 128, n_s = (N + 31) / 32;
-    // shared-memory budget from the largest box
-    const int K1max = 2 * p->box_max_x, K2max = 2 * p->box_max_y, N1max = P * p->box_max_y;
+    const int n_kb = (N + 127) / 128, n_s = (N + 31) / 32;
+    // shared-memory budget from the largest box; two tile buffers when they fit
+    const int K1max = pad64(2 * p->box_max_x), K2max = pad64(2 * p->box_max_y), N1max = P * p->box_max_y;
     if (N1max > 256) {
         p->last_error = "tensor path: occupied grid too tall (pols x rows > 256)";
         return EPIC_ERR_UNSUPPORTED;
     }
-    size_t off = 0;
-    const size_t sA1 = off;
-    off = align_up(off + 256ull * K1max, 1024);
-    const size_t sA2 = off;
-    off = align_up(off + 256ull * K2max, 1024);
-    const size_t sB1 = off;
-    off = align_up(off + 2ull * N1max * K1max, 1024);
-    const size_t sB2 = off;
-    off = align_up(off + 2ull * P * 64 * K2max, 1024);
-    size_t smem = std::max<size_t>(off, 120 * 1024);  // one CTA per SM (it owns all 512 TMEM columns)
-    if ((int)smem > p->smem_optin - 1024) {
+    const size_t b1 = align_up(2ull * N1max * K1max, 1024);
+    auto layout = [&](int nb, size_t* sA1, size_t* sA2, size_t* sB1, size_t* sB2) {
+        size_t off = 0;
+        *sA1 = off;
+        off = align_up(off + 256ull * K1max, 1024);
+        *sA2 = off;
+        off = align_up(off + 256ull * K2max, 1024);
+        *sB1 = off;
+        off += nb * b1;
+        *sB2 = off;
+        off = align_up(off + 2ull * 64 * P * K2max, 1024);
+        return off;
+    };
+    size_t sA1, sA2, sB1, sB2;
+    const size_t limit = (size_t)p->smem_optin - 2048;
+    // fast variant: 2 D1 slots + A2 (FP16 pairs) in TMEM columns [0, 256); 3 tiles + 2 B2 in shared memory
+    {
+        const int tm = 2 * N1max + p->box_max_y;  // 2 N1 + K2/2 columns
+        const size_t b2 = align_up(2ull * 64 * P * K2max, 1024);
+        const size_t need_fast = align_up(256ull * K1max, 1024) + 3 * b1 + 2 * b2;
+        p->tc.fast = tm <= 256 && need_fast <= limit;
+        if (p->tc.fast) {
+            p->tc.sA1 = 0;
+            p->tc.sB1 = (unsigned)align_up(256ull * K1max, 1024);
+            p->tc.sB2 = (unsigned)(p->tc.sB1 + 3 * b1);
+            p->tc.b1_bytes = (unsigned)b1;
+            p->tc.b2_bytes = (unsigned)b2;
+            p->tc.d1_cols = N1max;
+            p->tc.smem = (int)std::max<size_t>(need_fast + 1024, 120 * 1024);
+        }
+    }
+    int nb = 2;
+    size_t need = layout(2, &sA1, &sA2, &sB1, &sB2);
+    if (need > limit) {
+        nb = 1;
+        need = layout(1, &sA1, &sA2, &sB1, &sB2);
+    }
+    if (need > limit) {
         p->last_error = "tensor path: occupied grid too large for shared memory";
         return EPIC_ERR_UNSUPPORTED;
     }
-    p->tc.smem = (int)smem;
-    p->tc.sA1 = (unsigned)sA1;
-    p->tc.sA2 = (unsigned)sA2;
-    p->tc.sB1 = (unsigned)sB1;
-    p->tc.sB2 = (unsigned)sB2;
-    p->tc.n_g = n_g;
+    // +1 KB to align the operand base at run time; at least 120 KB so that one CTA
+    // per SM owns all 512 TMEM columns
+    const size_t smem = std::max<size_t>(need + 1024, 120 * 1024);
+    if (!p->tc.fast) {
+        p->tc.smem = (int)smem;
+        p->tc.sA1 = (unsigned)sA1;
+        p->tc.sA2 = (unsigned)sA2;
+        p->tc.sB1 = (unsigned)sB1;
+        p->tc.sB2 = (unsigned)sB2;
+        p->tc.b1_bytes = (unsigned)b1;
+    }
+    p->tc.nb = nb;
+    p->tc.n_g = n_s;
     p->tc.n_kb = n_kb;
     p->tc.n_s = n_s;
 
-    // DFT operand tables in the K-major core-matrix layout (FP64 -> FP16)
-    std::vector<long long> a1_off((size_t)C * n_g), a2_off((size_t)C * n_kb);
+    // DFT operand tables in the K-major core-matrix layout (FP64 -> FP16).
+    // A1 per (channel, 32-column slab s): rows 0..31 re, 32..63 im of kx = 32 s + j.
+    std::vector<long long> a1_off((size_t)C * n_s), a2_off((size_t)C * n_kb);
     size_t n1 = 0, n2 = 0;
     for (int c = 0; c < C; ++c) {
-        for (int g = 0; g < n_g; ++g) {
-            a1_off[(size_t)c * n_g + g] = (long long)n1;
-            n1 += 128ull * 2 * p->box[c].nx;
+        for (int sl = 0; sl < n_s; ++sl) {
+            a1_off[(size_t)c * n_s + sl] = (long long)n1;
+            n1 += 128ull * pad64(2 * p->box[c].nx);
         }
         for (int kb = 0; kb < n_kb; ++kb) {
             a2_off[(size_t)c * n_kb + kb] = (long long)n2;
-            n2 += 128ull * 2 * p->box[c].ny;
+            n2 += 128ull * pad64(2 * p->box[c].ny);
         }
     }
     std::vector<uint16_t> a1(n1, 0), a2(n2, 0);
@@ -437,10 +838,10 @@ epic_status dftgemm_setup(epic_plan_s* p)
     for (int c = 0; c < C; ++c) {
         const Box b = p->box[c];
         const int K1 = 2 * b.nx, K2 = 2 * b.ny;
-        for (int g = 0; g < n_g; ++g) {
-            uint16_t* t = &a1[a1_off[(size_t)c * n_g + g]];
-            for (int r = 0; r < 128; ++r) {
-                const int q = r / 64, kx = 64 * g + r % 64;
+        for (int sl = 0; sl < n_s; ++sl) {
+            uint16_t* t = &a1[a1_off[(size_t)c * n_s + sl]];
+            for (int r = 0; r < 64; ++r) {
+                const int q = r / 32, kx = 32 * sl + r % 32;
                 if (kx >= N) continue;
                 for (int k = 0; k < K1; ++k) {
                     const int x = b.x0 + (k % b.nx);
@@ -449,7 +850,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     double v;
                     if (q == 0) v = k < b.nx ? fr : -fi;
                     else v = k < b.nx ? fi : fr;
-                    t[core_off(r, k, K1)] = f16_bits(v);
+                    t[sw_off(r, k, 128)] = f16_bits(v);
                 }
             }
         }
@@ -462,12 +863,47 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     const int y = b.y0 + (k % b.ny);
                     double fr, fi;
                     F(y, ky, &fr, &fi);
-                    t[core_off(r, k, K2)] = f16_bits(k < b.ny ? fr : fi);
+                    t[sw_off(r, k, 128)] = f16_bits(k < b.ny ? fr : fi);
+                }
+            }
+        }
+    }
+    // row-major stage-2 operand as packed FP16 pairs (lower K in the low half) for TMEM
+    std::vector<long long> a2w_off((size_t)C * n_kb);
+    size_t nw = 0;
+    for (int c = 0; c < C; ++c)
+        for (int kb = 0; kb < n_kb; ++kb) {
+            a2w_off[(size_t)c * n_kb + kb] = (long long)nw;
+            nw += 128ull * p->box[c].ny;  // K2/2 words per row
+        }
+    std::vector<uint32_t> a2w(nw, 0);
+    for (int c = 0; c < C; ++c) {
+        const Box b = p->box[c];
+        for (int kb = 0; kb < n_kb; ++kb) {
+            uint32_t* t = &a2w[a2w_off[(size_t)c * n_kb + kb]];
+            for (int r = 0; r < 128; ++r) {
+                const int ky = 128 * kb + r;
+                if (ky >= N) continue;
+                for (int j = 0; j < b.ny; ++j) {
+                    uint16_t h[2];
+                    for (int u = 0; u < 2; ++u) {
+                        const int k = 2 * j + u;
+                        const int y = b.y0 + (k % b.ny);
+                        double fr, fi;
+                        F(y, ky, &fr, &fi);
+                        h[u] = f16_bits(k < b.ny ? fr : fi);
+                    }
+                    t[(size_t)r * b.ny + j] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
                 }
             }
         }
     }
     cudaError_t e = cudaMalloc(&p->tc.a1, n1 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w, nw * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(p->tc.a2w, a2w.data(), nw * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w_off, a2w_off.size() * sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->tc.a2w_off, a2w_off.data(), a2w_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->tc.a1, a1.data(), n1 * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2, n2 * 2);
     if (e == cudaSuccess) e = cudaMemcpy(p->tc.a2, a2.data(), n2 * 2, cudaMemcpyHostToDevice);
@@ -482,9 +918,15 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e != cudaSuccess) return cuda_fail(p, e, "tensor path table upload");
     p->dt.dft_bytes = (n1 + n2) * 2 + (a1_off.size() + a2_off.size()) * sizeof(long long);
 
+    // algorithmic work of the pruned DFT-as-GEMM per time sample (all channels, pols):
+    // complex MACs  nyp*nxp*N (rows along x) + N*nyp*N (columns along y), 8 flops each
+    double fl = 0.0;
+    for (int c = 0; c < C; ++c) fl += 8.0 * P * ((double)p->box[c].ny * p->box[c].nx * N + (double)N * p->box[c].ny * N);
+    p->tc_flops_per_sample = fl;
+
     // chunking: channel groups big enough to fill the GPU, time chunks whose tiles fit the budget
     size_t stride = 0;
-    for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * 2 * p->box[c].nx * 2);
+    for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
     const int per_ch = n_kb * n_s;
     int cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
@@ -498,16 +940,26 @@ epic_status dftgemm_setup(epic_plan_s* p)
     e = cudaMalloc(&p->scratch, p->scratch_bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(tensor path tile buffer)");
 
-    const size_t sg = sizeof(float2) * (size_t)p->A * P;
-    if (sg > 48 * 1024) {
-        if ((int)sg > p->smem_optin) {
-            p->last_error = "tensor path: frame of A*P voltages does not fit in shared memory";
-            return EPIC_ERR_UNSUPPORTED;
-        }
-        e = cudaFuncSetAttribute(k_dftgemm_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sg);
-        if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
+    // gridding kernel: cell lists in shared memory when the GCF is real and they fit
+    size_t max_list = 0;
+    int max_cells = 0;
+    for (int c = 0; c < C; ++c) max_cells = std::max(max_cells, p->box[c].nx * p->box[c].ny);
+    max_list = (size_t)p->A * p->K * p->K;
+    const size_t sv_bytes = sizeof(float2) * (size_t)p->A * P;
+    const size_t csr_bytes = sizeof(int) * (size_t)((max_cells + 2) & ~1) + sizeof(int2) * max_list;
+    p->tc.grid_csr_smem = p->gcf.kind == EPIC_GCF_GAUSSIAN && (int)(sv_bytes + csr_bytes) <= p->smem_optin;
+    p->tc.grid_smem = (int)(sv_bytes + (p->tc.grid_csr_smem ? csr_bytes : 0));
+    if (p->tc.grid_smem > p->smem_optin) {
+        p->last_error = "tensor path: frame of A*P voltages does not fit in shared memory";
+        return EPIC_ERR_UNSUPPORTED;
     }
-    e = cudaFuncSetAttribute(k_dftgemm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    e = cudaFuncSetAttribute(k_dftgemm_grid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dftgemm_grid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
+    e = cudaFuncSetAttribute(k_dftgemm_mma_fast<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_mma)");
     return EPIC_OK;
 }
@@ -515,7 +967,6 @@ epic_status dftgemm_setup(epic_plan_s* p)
 epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate)
 {
     const int C = p->C, P = p->P, A = p->A;
-    const size_t sg = sizeof(float2) * (size_t)A * P;
     MmaArgs a{};
     a.tiles = (const uint8_t*)p->scratch;
     a.tile_stride = p->tc.stride;
@@ -536,22 +987,37 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     a.sA2 = p->tc.sA2;
     a.sB1 = p->tc.sB1;
     a.sB2 = p->tc.sB2;
+    a.b1_bytes = p->tc.b1_bytes;
+    a.a2w = p->tc.a2w;
+    a.a2w_off = p->tc.a2w_off;
+    a.b2_bytes = p->tc.b2_bytes;
+    a.d1_cols = p->tc.d1_cols;
+    const int fpc = kGridFramesPerBlock;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
         const int ng = std::min(p->tc.cg, C - c0);
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
+            const dim3 gg((nt + fpc - 1) / fpc, ng);
             ev_begin(p, "k_dftgemm_grid", s);
-            k_dftgemm_grid<<<dim3(nt, ng), kThreads, sg, s>>>(volt, t0, c0, ng, C, A, P, p->dt.box, p->dt.cell_off,
-                                                            p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w,
-                                                            (uint8_t*)p->scratch, p->tc.stride);
+            if (p->tc.grid_csr_smem)
+                k_dftgemm_grid<true><<<gg, kThreads, p->tc.grid_smem, s>>>(
+                    volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box, p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,
+                    p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride);
+            else
+                k_dftgemm_grid<false><<<gg, kThreads, p->tc.grid_smem, s>>>(
+                    volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box, p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,
+                    p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride);
             ev_end(p, s);
             a.c0 = c0;
             a.n_ch = ng;
             a.nt = nt;
             a.accumulate = (accumulate || t0 > 0) ? 1 : 0;
             const int items = ng * a.n_kb * a.n_s;
+            const int grid = std::min(items, p->sm_count);
             ev_begin(p, "k_dftgemm_mma", s);
-            k_dftgemm_mma<<<std::min(items, p->sm_count), kThreads, p->tc.smem, s>>>(a);
+            if (p->tc.fast) k_dftgemm_mma_fast<0><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
+            else if (p->tc.nb == 2) k_dftgemm_mma<2><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
+            else k_dftgemm_mma<1><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             ev_end(p, s);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(p, e, "tensor path launch");

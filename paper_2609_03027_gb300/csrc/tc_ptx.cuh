@@ -94,6 +94,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, absolute LBO mode off, swizzle none
 }
 
+// Shared-memory matrix descriptor for the 128-byte swizzled K-major layout:
+// rows of 128 bytes (64 halves of K), 8-row atoms of 1024 bytes (sbo), the
+// 16-byte chunk c of row r stored at chunk position c ^ (r & 7).  The operand
+// base must be 1024-byte aligned; a K step of 16 halves advances the start
+// address by 32 bytes inside the atom, a 64-wide K panel by rows * 128 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: one 8-row atom
+    d |= (uint64_t)1 << 46;             // descriptor version of the tcgen05 family
+    d |= (uint64_t)2 << 61;             // layout: 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D f32, A and B f16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
 {
@@ -115,6 +131,28 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+
+// D[tmem] (+)= A[tmem] * B[smem]^T: A read from tensor memory (rows = lanes, K
+// halves packed two per 32-bit column, lower K in the low half), issued by one thread.
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 8 consecutive 32-bit TMEM columns of this thread's lane <- r[0..7]
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Arrive once on `bar` when every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar)

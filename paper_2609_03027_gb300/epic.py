@@ -62,7 +62,8 @@ class _PlanDesc(ctypes.Structure):
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("n_prod", ctypes.c_int), ("box_max_x", ctypes.c_int),
                 ("box_max_y", ctypes.c_int), ("time_chunk", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
-                ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int)]
+                ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int),
+                ("gemm_flops_per_sample", ctypes.c_double)]
 
 
 _lock = threading.Lock()
