@@ -47,11 +47,16 @@ struct TcState {
     int nb = 1;                    // tile buffers (2 = next tile prefetched)
     int grid_smem = 0;             // dynamic shared memory of the gridding kernel
     bool grid_csr_smem = false;    // gridding kernel stages the cell lists in shared memory
+    int grid_frames = 1;           // frames gridded per pass by the gridding kernel
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2
     uint32_t* a2w = nullptr;       // stage-2 operand rows as packed FP16 pairs (fast variant)
     long long* a2w_off = nullptr;
     unsigned b2_bytes = 0;
     int d1_cols = 0;
+    bool ws = false;               // warp-specialised 64-column-pair kernel
+    uint16_t* a1p = nullptr;       // stage-1 operands per (channel, 64-column kx pair)
+    long long* a1p_off = nullptr;
+    int n_gp = 0;                  // 64-column pairs per channel
 };
 
 struct KernelEvent {

@@ -101,6 +101,9 @@ struct MmaArgs {
     const long long* a2w_off;   // word offsets into a2w
     unsigned b2_bytes;          // bytes per B2 buffer
     int d1_cols;                // TMEM columns per D1 slot
+    // warp-specialised variant only
+    const uint16_t* a1p;        // stage-1 operands per (channel, 64-column kx pair)
+    const long long* a1p_off;
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -157,10 +160,14 @@ __device__ __forceinline__ void store_pixels16(float* op, int nk, int accumulate
 }
 
 // Unpack and gather-grid frames of one chunk into FP16 UMMA tiles.  A block
-// handles `fpc` consecutive frames of one channel so that the channel's cell
-// lists are read once; with CSR_SMEM they are staged in shared memory as
-// (element, real weight) pairs (Gaussian GCF), otherwise read through L1.
-template <bool CSR_SMEM>
+// handles `fpc` consecutive frames of one channel, F frames per pass; a thread
+// owns two horizontally adjacent cells, walks their (element, weight) lists once
+// per pass and applies every entry to the F frames (F independent accumulators),
+// then writes the cells as FP16 pairs: consecutive threads cover consecutive
+// cell pairs of a row, so a warp fills whole 128-byte rows of the swizzled tile.
+// With CSR_SMEM the channel's cell lists sit in shared memory as (element, real
+// weight) pairs (Gaussian GCF), otherwise they are read through L1.
+template <bool CSR_SMEM, int F>
 __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __restrict__ volt, int t0, int c0,
                                                            int n_ch, int nt, int fpc, int C, int A, int P,
                                                            const int4* __restrict__ box,
@@ -171,62 +178,88 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                                                            unsigned long long tile_stride)
 {
     extern __shared__ __align__(16) uint8_t gsm[];
-    float2* sv = reinterpret_cast<float2*>(gsm);  // [A][P]
+    float4* sv = reinterpret_cast<float4*>(gsm);  // [F][A]: (re X, im X, re Y, im Y)
     const int cl = blockIdx.y, c = c0 + cl;
     const int4 b = box[c];
     const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
     const int* gptr = cell_ptr + cell_off[c];
     const int* ptr = gptr;
     int2* con = nullptr;
-    int base = 0;
     if (CSR_SMEM) {
-        int* sptr = reinterpret_cast<int*>(gsm + sizeof(float2) * (size_t)A * P);
+        int* sptr = reinterpret_cast<int*>(gsm + sizeof(float4) * (size_t)F * A);
         con = reinterpret_cast<int2*>(sptr + ((ncell + 2) & ~1));
-        base = gptr[0];
+        const int base = gptr[0];
         const int ncon = gptr[ncell] - base;
         for (int i = threadIdx.x; i <= ncell; i += blockDim.x) sptr[i] = gptr[i] - base;
-        for (int i = threadIdx.x; i < ncon; i += blockDim.x) con[i] = make_int2(ce[base + i], __float_as_int(cw[base + i].x));
+        for (int i = threadIdx.x; i < ncon; i += blockDim.x)
+            con[i] = make_int2(ce[base + i], __float_as_int(cw[base + i].x));
         ptr = sptr;
     }
     const int f0 = blockIdx.x * fpc, f1 = min(nt, f0 + fpc);
-    const int tasks = nyp * (nxp >> 3);
-    for (int tl = f0; tl < f1; ++tl) {
+    const int half = nxp >> 1;
+    const int tasks = nyp * half;
+    for (int tb = f0; tb < f1; tb += F) {
+        const int nf = min(F, f1 - tb);
         __syncthreads();
-        const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
-        for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = unpack44(fr[i]);
+        for (int i = threadIdx.x; i < nf * A; i += blockDim.x) {
+            const int f = i / A, e = i - f * A;
+            const uint8_t* fr = volt + ((size_t)(t0 + tb + f) * C + c) * (size_t)A * P + (size_t)e * P;
+            const float2 x = unpack44(fr[0]);
+            const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+            sv[f * A + e] = make_float4(x.x, x.y, y.x, y.y);
+        }
         __syncthreads();
-        uint8_t* tile = tiles + ((size_t)tl * n_ch + cl) * tile_stride;
         for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
-            const int y = task % nyp, x8 = task / nyp;
-            const int r0 = y * nxp + x8 * 8;
-            float2 gx[8], gy[8];
+            const int y = task / half, x = 2 * (task - y * half);
+            float4 g[2][F];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                gx[i] = make_float2(0.f, 0.f);
-                gy[i] = make_float2(0.f, 0.f);
-                const int q1 = ptr[r0 + i + 1];
-                for (int q = ptr[r0 + i]; q < q1; ++q) {
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) g[j][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const int r = y * nxp + x + j;
+                const int q1 = ptr[r + 1];
+                for (int q = ptr[r]; q < q1; ++q) {
+                    int e;
+                    float2 w;
                     if (CSR_SMEM) {
                         const int2 cr = con[q];
-                        const float w = __int_as_float(cr.y);
-                        const float2 vx = sv[cr.x * P];
-                        gx[i].x = fmaf(w, vx.x, gx[i].x);
-                        gx[i].y = fmaf(w, vx.y, gx[i].y);
-                        if (P == 2) {
-                            const float2 vy = sv[cr.x * P + 1];
-                            gy[i].x = fmaf(w, vy.x, gy[i].x);
-                            gy[i].y = fmaf(w, vy.y, gy[i].y);
-                        }
+                        e = cr.x;
+                        w = make_float2(__int_as_float(cr.y), 0.f);
                     } else {
-                        const int e = ce[q];
-                        const float2 w = cw[q];
-                        gx[i] = cfma(w, sv[e * P], gx[i]);
-                        if (P == 2) gy[i] = cfma(w, sv[e * P + 1], gy[i]);
+                        e = ce[q];
+                        w = cw[q];
+                    }
+#pragma unroll
+                    for (int f = 0; f < F; ++f) {
+                        const float4 v = sv[f * A + e];
+                        if (CSR_SMEM) {
+                            g[j][f].x = fmaf(w.x, v.x, g[j][f].x);
+                            g[j][f].y = fmaf(w.x, v.y, g[j][f].y);
+                            g[j][f].z = fmaf(w.x, v.z, g[j][f].z);
+                            g[j][f].w = fmaf(w.x, v.w, g[j][f].w);
+                        } else {
+                            const float2 gx = cfma(w, make_float2(v.x, v.y), make_float2(g[j][f].x, g[j][f].y));
+                            const float2 gy = cfma(w, make_float2(v.z, v.w), make_float2(g[j][f].z, g[j][f].w));
+                            g[j][f] = make_float4(gx.x, gx.y, gy.x, gy.y);
+                        }
                     }
                 }
             }
-            store_tile_row(tile, 0 * nyp + y, N1, nxp, x8, gx);
-            if (P == 2) store_tile_row(tile, 1 * nyp + y, N1, nxp, x8, gy);
+            // cells (y, x) and (y, x+1): K index x (re) and nxp + x (im), rows p*nyp + y
+            const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nf) break;
+                uint8_t* tile = tiles + ((size_t)(tb + f) * n_ch + cl) * tile_stride;
+                const int R0 = y;
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_re, N1) + within) = pack_h2(g[0][f].x, g[1][f].x);
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_im, N1) + within) = pack_h2(g[0][f].y, g[1][f].y);
+                if (P == 2) {
+                    const int R1 = nyp + y;
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1) + within) = pack_h2(g[0][f].z, g[1][f].z);
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1) + within) = pack_h2(g[0][f].w, g[1][f].w);
+                }
+            }
         }
     }
 }
@@ -745,6 +778,331 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_dftgemm_mma_fast(MmaArgs a)
     if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
 }
 
+// ---------------------------------------------------------------------------------
+// Warp-specialised variant: a work item is (channel, 128-row ky block, 64-column kx
+// pair), so stage 1 uses all 128 rows (re and im of 64 kx) and stage 2 runs as two
+// N = 64 P halves (kx 0..31 and 32..63 of the pair).  16 warps do the epilogues;
+// three lanes issue the tensor core work and the tile copies; all hand-offs go
+// through mbarriers, never a block-wide barrier inside the frame loop:
+//   d1_full[s]  commit after S1 into D1[s]          (waited by every warp)
+//   b2_full[s]  16 warp arrivals after epilogue 1   (waited by the three issuers)
+//   d2_full[h]  commit after S2 of half h           (waited by every warp)
+//   d2_empty[h] 8 warp arrivals after epilogue 2 h  (waited by the issuer of h)
+//   tile[b]     TMA completion of grid tile buffer b
+// Per frame t every warp: wait S1(t) -> (issuer B: copy tile t+2) -> epilogue 1 (t)
+// into B2[t&1] -> arrive b2_full -> wait S2(t-1) -> epilogue 2 (t-1) -> arrive
+// d2_empty; issuers then queue S2a(t), S2b(t) (after b2_full(t) and d2_empty(t-1))
+// and S1(t+2) (after b2_full(t) frees D1[t&1] and tile t+2 has landed).
+// TMEM: D1[0..1] at 0 and d1_cols, A2 at 2 d1_cols, D2 half h at 256 + 128 h.
+constexpr int kWsThreads = 512;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Epilogue 1 of one warp: the stage-1 result in this warp's lane quarter (lanes =
+// 32 kx of half h; part 0 = Hr, part 1 = Hi), columns [c0, c1) of pol p, written to
+// the B2 rows of half h / pol p (row kx = [Hr | -Hi], row 32+kx = [Hi | Hr]).
+__device__ __forceinline__ void ws_epilogue1(uint32_t taddr, int nyp, int yc0, int yc1, bool imw, int lane,
+                                             uint8_t* b2, int row0, int R2)
+{
+    const int n0 = row0 + lane, n1 = row0 + 32 + lane;
+    for (int yb = yc0; yb < yc1; yb += 2) {
+        const int ng = min(2, yc1 - yb);
+        uint32_t r[16];
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            if (g < ng) tmem_ld8(taddr + 8 * (yb + g), r + 8 * g);
+        tc::tmem_wait_ld(r);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (g >= ng) break;
+            uint4 pos, neg;
+            pos.x = pack_h2(__uint_as_float(r[8 * g + 0]), __uint_as_float(r[8 * g + 1]));
+            pos.y = pack_h2(__uint_as_float(r[8 * g + 2]), __uint_as_float(r[8 * g + 3]));
+            pos.z = pack_h2(__uint_as_float(r[8 * g + 4]), __uint_as_float(r[8 * g + 5]));
+            pos.w = pack_h2(__uint_as_float(r[8 * g + 6]), __uint_as_float(r[8 * g + 7]));
+            neg.x = pos.x ^ 0x80008000u;
+            neg.y = pos.y ^ 0x80008000u;
+            neg.z = pos.z ^ 0x80008000u;
+            neg.w = pos.w ^ 0x80008000u;
+            const int kc_lo = yb + g, kc_hi = (nyp >> 3) + kc_lo;
+            if (!imw) {
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_lo, R2)) = pos;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_hi, R2)) = pos;
+            } else {
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_hi, R2)) = neg;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_lo, R2)) = pos;
+            }
+        }
+    }
+}
+
+// Epilogue 2 of one warp: 16 kx x (X, Y) of its 32 ky rows, 4 kx per TMEM batch.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ws_epilogue2(uint32_t taddr, int P, float (&axx)[16], float (&ayy)[16],
+                                             float (&arx)[16], float (&aix)[16])
+{
+#pragma unroll
+    for (int hb = 0; hb < 4; ++hb) {
+        uint32_t xr[4], xi[4], yr[4], yi[4];
+        tmem_ld4(taddr + 4 * hb, xr);
+        tmem_ld4(taddr + 32 + 4 * hb, xi);
+        if (P == 2) {
+            tmem_ld4(taddr + 64 + 4 * hb, yr);
+            tmem_ld4(taddr + 96 + 4 * hb, yi);
+        }
+        tc::tmem_wait_ld(xr);
+        tc::tmem_wait_ld(xi);
+        if (P == 2) {
+            tc::tmem_wait_ld(yr);
+            tc::tmem_wait_ld(yi);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int o = 4 * hb + i;
+            const float Xr = __uint_as_float(xr[i]), Xi = __uint_as_float(xi[i]);
+            axx[o] = fmaf(Xr, Xr, fmaf(Xi, Xi, axx[o]));
+            if (P == 2) {
+                const float Yr = __uint_as_float(yr[i]), Yi = __uint_as_float(yi[i]);
+                ayy[o] = fmaf(Yr, Yr, fmaf(Yi, Yi, ayy[o]));
+                arx[o] = fmaf(Xr, Yr, fmaf(Xi, Yi, arx[o]));
+                aix[o] = fmaf(Xi, Yr, fmaf(-Xr, Yi, aix[o]));
+            }
+        }
+    }
+}
+
+template <int dummy>
+__global__ void __launch_bounds__(kWsThreads, 1) k_dftgemm_ws(MmaArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar_a, d1_full[2], b2_full[2], d2_full[2], d2_empty[2], tile_full[2];
+    __shared__ uint32_t tmem_sh;
+    __shared__ int err_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool isB = tid == 5 * 32;    // stage 1 + tile copies (sub-partition 1)
+    const bool isA = tid == 2 * 32;    // stage 2, kx half 0 (sub-partition 2)
+    const bool isC = tid == 15 * 32;   // stage 2, kx half 1 (sub-partition 3)
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_sh, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_a, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&d1_full[i], 1);
+            tc::mbar_init(&b2_full[i], 16);
+            tc::mbar_init(&d2_full[i], 1);
+            tc::mbar_init(&d2_empty[i], 8);
+            tc::mbar_init(&tile_full[i], 1);
+        }
+        err_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_sh;
+    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+    uint8_t* sA1 = sbase + a.sA1;
+    // parities (bit s per slot); every thread waits each phase it tracks exactly once
+    uint32_t ph_d1 = 0, ph_d2 = 0, ph_b2 = 0, ph_e2 = 0, ph_tile = 0, ph_a = 0;
+    bool ok = true;
+    const int P = a.P;
+    const int q4 = warp & 3, j4 = warp >> 2;       // lane quarter, column group
+    const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+    const int R2 = 2 * 64 * P;                      // B2 rows: half h at 64 P h, pol p at 64 p
+    const uint32_t a2col = 2u * a.d1_cols;
+    const int items = a.n_ch * a.n_kb * a.n_g;
+    // epilogue-2 part of this warp: quarter q4 (ky), kx group j4 -> half h2, 16 kx at 16 (j4 & 1)
+    const int h2 = j4 >> 1;
+
+    for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
+        const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
+        const int c = a.c0 + cl;
+        const int4 bx = a.box[c];
+        const int nxp = bx.z, nyp = bx.w;
+        const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
+        const int K1s = pad64(K1);
+        const uint32_t a1_bytes = 256u * K1s;
+        const uint32_t tile_bytes = (uint32_t)N1 * K1s * 2;
+        const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
+        const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+        const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 64 * P);
+        const int nt = a.nt;
+
+        auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
+            const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
+            ph ^= 1u << slot;
+            if (!r) err_sh = 1;
+            return r;
+        };
+        auto load_tile = [&](int t) {
+            const int b = t & 1;
+            tc::mbar_expect_tx(&tile_full[b], tile_bytes);
+            tc::bulk_g2s(sbase + a.sB1 + (size_t)b * a.b1_bytes, tiles_c + (size_t)t * frame_step, tile_bytes,
+                         &tile_full[b]);
+        };
+        auto issue_s1 = [&](int t) {  // issuer B: tile t (buffer t&1) -> D1[t&1]
+            issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
+                     tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
+            tc::mma_commit(&d1_full[t & 1]);
+        };
+        auto issue_s2 = [&](int t, int h) {  // issuers A / C: B2[t&1] half h -> D2 half h
+            const uint32_t b2 = tc::smem_u32(sbase + a.sB2 + (size_t)(t & 1) * a.b2_bytes) + (uint32_t)(64 * P * h) * 128;
+            issue_ts(K2 / 16, tmem + 256 + 128 * h, tmem + a2col, b2, R2 * 128, id2);
+            tc::mma_commit(&d2_full[h]);
+        };
+
+        // ---- item prologue
+        if (isB) {
+            tc::mbar_expect_tx(&bar_a, a1_bytes);
+            tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
+            for (int j = 0; j < 2 && j < nt; ++j) load_tile(j);
+        }
+        __syncwarp();
+        if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
+            const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
+            for (int jj = 0; jj < K2 / 2; jj += 8) {
+                uint32_t r[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
+                tc::tmem_st8(tmem + lane_base + a2col + jj, r);
+            }
+            tc::tmem_wait_st();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (isB) {
+            if (wait_bit(&bar_a, ph_a, 0)) {
+                for (int j = 0; j < 2 && j < nt; ++j)
+                    if (wait_bit(&tile_full[j], ph_tile, j)) {
+                        tc::fence_after_sync();
+                        issue_s1(j);
+                    }
+            }
+        }
+        __syncwarp();
+
+        float axx[16], ayy[16], arx[16], aix[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+
+        for (int t = 0; t < nt; ++t) {
+            const int sl = t & 1;
+            // (1) S1(t) complete
+            bool w = wait_bit(&d1_full[sl], ph_d1, sl);
+            __syncwarp();
+            tc::fence_after_sync();
+            // (2) issuer B: the tile buffer of S1(t) is free -> copy tile t+2
+            if (isB && t + 2 < nt) load_tile(t + 2);
+            __syncwarp();
+            // (3) epilogue 1 (t): quarter q4 (half q4&1, part q4>>1); columns of pol / y-range by j4
+            if (w) {
+                const int hh = q4 & 1;
+                const bool imw = (q4 >> 1) != 0;
+                const int nyc = nyp >> 3;
+                int p, yc0, yc1;
+                if (P == 2) {
+                    p = j4 >> 1;
+                    const int mid = (nyc + 1) >> 1;
+                    yc0 = (j4 & 1) ? mid : 0;
+                    yc1 = (j4 & 1) ? nyc : mid;
+                } else {
+                    p = 0;
+                    yc0 = (nyc * j4) >> 2;
+                    yc1 = (nyc * (j4 + 1)) >> 2;
+                }
+                ws_epilogue1(tmem + lane_base + sl * a.d1_cols + p * nyp, nyp, yc0, yc1, imw, lane,
+                             sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * P * hh + 64 * p, R2);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&b2_full[sl]);
+            // (4) epilogue 2 (t-1) after S2(t-1) of both halves
+            if (t >= 1) {
+                const bool wa = wait_bit(&d2_full[0], ph_d2, 0);
+                const bool wb = wait_bit(&d2_full[1], ph_d2, 1);
+                __syncwarp();
+                tc::fence_after_sync();
+                if (wa && wb)
+                    ws_epilogue2(tmem + lane_base + 256 + 128 * h2 + 16 * (j4 & 1), P, axx, ayy, arx, aix);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&d2_empty[h2]);
+            }
+            // (5) issuers
+            if (isA || isC) {
+                const int h = isA ? 0 : 1;
+                bool r = wait_bit(&b2_full[sl], ph_b2, sl);
+                if (t >= 1) r = wait_bit(&d2_empty[h], ph_e2, h) && r;
+                if (r) {
+                    tc::fence_after_sync();
+                    issue_s2(t, h);
+                } else {
+                    tc::mma_commit(&d2_full[h]);
+                }
+            }
+            if (isB && t + 2 < nt) {
+                bool r = wait_bit(&b2_full[sl], ph_b2, sl);  // every warp has read D1[sl]
+                r = wait_bit(&tile_full[sl], ph_tile, sl) && r;
+                if (r) {
+                    tc::fence_after_sync();
+                    issue_s1(t + 2);
+                } else {
+                    tc::mma_commit(&d1_full[sl]);
+                }
+            } else if (isB) {
+                wait_bit(&b2_full[sl], ph_b2, sl);  // keep the phase count in step
+            }
+            __syncwarp();
+            if (__any_sync(0xffffffffu, err_sh != 0)) break;
+        }
+        // final epilogue 2 (nt-1)
+        if (nt > 0 && !err_sh) {
+            const bool wa = wait_bit(&d2_full[0], ph_d2, 0);
+            const bool wb = wait_bit(&d2_full[1], ph_d2, 1);
+            __syncwarp();
+            tc::fence_after_sync();
+            if (wa && wb)
+                ws_epilogue2(tmem + lane_base + 256 + 128 * h2 + 16 * (j4 & 1), P, axx, ayy, arx, aix);
+        }
+        tc::fence_before_sync();
+        ok = __syncthreads_and(err_sh == 0) != 0;
+        tc::fence_after_sync();
+        if (!ok) break;
+        // ---- images: row ky = 128 kb + 32 q4 + lane, 16 kx from 64 g + 32 h2 + 16 (j4 & 1)
+        const int ky = 128 * kb + 32 * q4 + lane;
+        const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
+        if (ky < a.N && kx0 < a.N) {
+            const size_t NN = (size_t)a.N * a.N;
+            float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
+            const int nk = min(16, a.N - kx0);
+            store_pixels16(o, nk, a.accumulate, axx);
+            if (a.nprod == 4) {
+                store_pixels16(o + NN, nk, a.accumulate, ayy);
+                store_pixels16(o + 2 * NN, nk, a.accumulate, arx);
+                store_pixels16(o + 3 * NN, nk, a.accumulate, aix);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
+}
+
 }  // namespace
 
 epic_status dftgemm_setup(epic_plan_s* p)
@@ -772,12 +1130,28 @@ epic_status dftgemm_setup(epic_plan_s* p)
     };
     size_t sA1, sA2, sB1, sB2;
     const size_t limit = (size_t)p->smem_optin - 2048;
+    // warp-specialised variant (64-column pairs): A1 + 2 tiles + 2 double-width B2 buffers
+    {
+        const int tm = 2 * N1max + p->box_max_y;
+        const size_t b2w = align_up(2ull * 2 * 64 * P * K2max, 1024);
+        const size_t need_ws = align_up(256ull * K1max, 1024) + 2 * b1 + 2 * b2w;
+        p->tc.ws = tm <= 256 && need_ws <= limit;
+        if (p->tc.ws) {
+            p->tc.sA1 = 0;
+            p->tc.sB1 = (unsigned)align_up(256ull * K1max, 1024);
+            p->tc.sB2 = (unsigned)(p->tc.sB1 + 2 * b1);
+            p->tc.b1_bytes = (unsigned)b1;
+            p->tc.b2_bytes = (unsigned)b2w;
+            p->tc.d1_cols = N1max;
+            p->tc.smem = (int)(need_ws + 1024);
+        }
+    }
     // fast variant: 2 D1 slots + A2 (FP16 pairs) in TMEM columns [0, 256); 3 tiles + 2 B2 in shared memory
     {
         const int tm = 2 * N1max + p->box_max_y;  // 2 N1 + K2/2 columns
         const size_t b2 = align_up(2ull * 64 * P * K2max, 1024);
         const size_t need_fast = align_up(256ull * K1max, 1024) + 3 * b1 + 2 * b2;
-        p->tc.fast = tm <= 256 && need_fast <= limit;
+        p->tc.fast = !p->tc.ws && tm <= 256 && need_fast <= limit;
         if (p->tc.fast) {
             p->tc.sA1 = 0;
             p->tc.sB1 = (unsigned)align_up(256ull * K1max, 1024);
@@ -801,7 +1175,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
     // +1 KB to align the operand base at run time; at least 120 KB so that one CTA
     // per SM owns all 512 TMEM columns
     const size_t smem = std::max<size_t>(need + 1024, 120 * 1024);
-    if (!p->tc.fast) {
+    if (!p->tc.fast && !p->tc.ws) {
         p->tc.smem = (int)smem;
         p->tc.sA1 = (unsigned)sA1;
         p->tc.sA2 = (unsigned)sA2;
@@ -868,6 +1242,35 @@ epic_status dftgemm_setup(epic_plan_s* p)
             }
         }
     }
+    // A1 per (channel, 64-column pair g): rows 0..63 re, 64..127 im of kx = 64 g + j
+    const int n_gp = (N + 63) / 64;
+    std::vector<long long> a1p_off((size_t)C * n_gp);
+    size_t n1p = 0;
+    for (int c = 0; c < C; ++c)
+        for (int g = 0; g < n_gp; ++g) {
+            a1p_off[(size_t)c * n_gp + g] = (long long)n1p;
+            n1p += 128ull * pad64(2 * p->box[c].nx);
+        }
+    std::vector<uint16_t> a1p(n1p, 0);
+    for (int c = 0; c < C; ++c) {
+        const Box b = p->box[c];
+        const int K1 = 2 * b.nx;
+        for (int g = 0; g < n_gp; ++g) {
+            uint16_t* t = &a1p[a1p_off[(size_t)c * n_gp + g]];
+            for (int r = 0; r < 128; ++r) {
+                const int q = r / 64, kx = 64 * g + r % 64;
+                if (kx >= N) continue;
+                for (int k = 0; k < K1; ++k) {
+                    const int x = b.x0 + (k % b.nx);
+                    double fr, fi;
+                    F(x, kx, &fr, &fi);
+                    const double v = q == 0 ? (k < b.nx ? fr : -fi) : (k < b.nx ? fi : fr);
+                    t[sw_off(r, k, 128)] = f16_bits(v);
+                }
+            }
+        }
+    }
+    p->tc.n_gp = n_gp;
     // row-major stage-2 operand as packed FP16 pairs (lower K in the low half) for TMEM
     std::vector<long long> a2w_off((size_t)C * n_kb);
     size_t nw = 0;
@@ -899,6 +1302,11 @@ epic_status dftgemm_setup(epic_plan_s* p)
         }
     }
     cudaError_t e = cudaMalloc(&p->tc.a1, n1 * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a1p, n1p * 2);
+    if (e == cudaSuccess) e = cudaMemcpy(p->tc.a1p, a1p.data(), n1p * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a1p_off, a1p_off.size() * sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->tc.a1p_off, a1p_off.data(), a1p_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w, nw * 4);
     if (e == cudaSuccess) e = cudaMemcpy(p->tc.a2w, a2w.data(), nw * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w_off, a2w_off.size() * sizeof(long long));
@@ -928,7 +1336,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
     size_t stride = 0;
     for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
-    const int per_ch = n_kb * n_s;
+    const int per_ch = n_kb * (p->tc.ws ? n_gp : n_s);
     int cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
     int tcn = (int)std::max<size_t>(1, kScratchBudget / ((size_t)cg * stride));
     tcn = std::min(tcn, p->max_time);
@@ -940,24 +1348,41 @@ epic_status dftgemm_setup(epic_plan_s* p)
     e = cudaMalloc(&p->scratch, p->scratch_bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(tensor path tile buffer)");
 
-    // gridding kernel: cell lists in shared memory when the GCF is real and they fit
-    size_t max_list = 0;
+    // gridding kernel: F frames per pass (4, 2 or 1 as the voltages fit), cell lists in
+    // shared memory when the GCF is real and they fit
     int max_cells = 0;
     for (int c = 0; c < C; ++c) max_cells = std::max(max_cells, p->box[c].nx * p->box[c].ny);
-    max_list = (size_t)p->A * p->K * p->K;
-    const size_t sv_bytes = sizeof(float2) * (size_t)p->A * P;
+    const size_t max_list = (size_t)p->A * p->K * p->K;
     const size_t csr_bytes = sizeof(int) * (size_t)((max_cells + 2) & ~1) + sizeof(int2) * max_list;
-    p->tc.grid_csr_smem = p->gcf.kind == EPIC_GCF_GAUSSIAN && (int)(sv_bytes + csr_bytes) <= p->smem_optin;
+    const size_t gl = (size_t)p->smem_optin;
+    int gf = 4;
+    while (gf > 1 && sizeof(float4) * (size_t)gf * p->A > gl / 2) gf >>= 1;
+    size_t sv_bytes = sizeof(float4) * (size_t)gf * p->A;
+    p->tc.grid_csr_smem = p->gcf.kind == EPIC_GCF_GAUSSIAN && sv_bytes + csr_bytes <= gl;
+    if (!p->tc.grid_csr_smem) {
+        while (gf > 1 && sizeof(float4) * (size_t)gf * p->A > gl) gf >>= 1;
+        sv_bytes = sizeof(float4) * (size_t)gf * p->A;
+    }
+    p->tc.grid_frames = gf;
     p->tc.grid_smem = (int)(sv_bytes + (p->tc.grid_csr_smem ? csr_bytes : 0));
     if (p->tc.grid_smem > p->smem_optin) {
         p->last_error = "tensor path: frame of A*P voltages does not fit in shared memory";
         return EPIC_ERR_UNSUPPORTED;
     }
-    e = cudaFuncSetAttribute(k_dftgemm_grid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dftgemm_grid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
+#define EPIC_GRID_ATTR(CS, FF)                                                                                      \
+    if (e == cudaSuccess)                                                                                           \
+        e = cudaFuncSetAttribute(k_dftgemm_grid<CS, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
+    e = cudaSuccess;
+    EPIC_GRID_ATTR(true, 4)
+    EPIC_GRID_ATTR(true, 2)
+    EPIC_GRID_ATTR(true, 1)
+    EPIC_GRID_ATTR(false, 4)
+    EPIC_GRID_ATTR(false, 2)
+    EPIC_GRID_ATTR(false, 1)
+#undef EPIC_GRID_ATTR
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
-    e = cudaFuncSetAttribute(k_dftgemm_mma_fast<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    e = cudaFuncSetAttribute(k_dftgemm_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma_fast<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_mma)");
@@ -992,30 +1417,42 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     a.a2w_off = p->tc.a2w_off;
     a.b2_bytes = p->tc.b2_bytes;
     a.d1_cols = p->tc.d1_cols;
+    a.a1p = p->tc.a1p;
+    a.a1p_off = p->tc.a1p_off;
     const int fpc = kGridFramesPerBlock;
+    const int F = p->tc.grid_frames;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
         const int ng = std::min(p->tc.cg, C - c0);
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
             ev_begin(p, "k_dftgemm_grid", s);
-            if (p->tc.grid_csr_smem)
-                k_dftgemm_grid<true><<<gg, kThreads, p->tc.grid_smem, s>>>(
-                    volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box, p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,
-                    p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride);
-            else
-                k_dftgemm_grid<false><<<gg, kThreads, p->tc.grid_smem, s>>>(
-                    volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box, p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,
-                    p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride);
+#define EPIC_GRID_LAUNCH(CS, FF)                                                                                    \
+    k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box,       \
+                                                              p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,         \
+                                                              p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride)
+            if (p->tc.grid_csr_smem) {
+                if (F == 4) EPIC_GRID_LAUNCH(true, 4);
+                else if (F == 2) EPIC_GRID_LAUNCH(true, 2);
+                else EPIC_GRID_LAUNCH(true, 1);
+            } else {
+                if (F == 4) EPIC_GRID_LAUNCH(false, 4);
+                else if (F == 2) EPIC_GRID_LAUNCH(false, 2);
+                else EPIC_GRID_LAUNCH(false, 1);
+            }
+#undef EPIC_GRID_LAUNCH
             ev_end(p, s);
             a.c0 = c0;
             a.n_ch = ng;
             a.nt = nt;
             a.accumulate = (accumulate || t0 > 0) ? 1 : 0;
-            const int items = ng * a.n_kb * a.n_s;
+            const int items = ng * a.n_kb * (p->tc.ws ? p->tc.n_gp : a.n_s);
             const int grid = std::min(items, p->sm_count);
-            ev_begin(p, "k_dftgemm_mma", s);
-            if (p->tc.fast) k_dftgemm_mma_fast<0><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
+            ev_begin(p, p->tc.ws ? "k_dftgemm_ws" : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
+            if (p->tc.ws) {
+                a.n_g = p->tc.n_gp;
+                k_dftgemm_ws<0><<<grid, kWsThreads, p->tc.smem, s>>>(a);
+            } else if (p->tc.fast) k_dftgemm_mma_fast<0><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             else if (p->tc.nb == 2) k_dftgemm_mma<2><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             else k_dftgemm_mma<1><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             ev_end(p, s);
