@@ -1,11 +1,241 @@
-// Fused FP32 path (placeholder until the fused kernel lands).
+// Fused FP32 path: one kernel per call runs, for every (channel, time sample,
+// pol), unpack -> gridding -> 2-D FFT -> polarisation products -> accumulation
+// (paper Sec. 2, Eq. 1-2), with the images of a work item accumulated in
+// registers over the whole block and written once.
+//
+// Work item = (channel c, slab of SW image columns kx).  Per frame:
+//   for each chunk of 16 occupied grid rows: gather-grid the chunk (both pols)
+//   into shared memory, FFT the rows (radix-2 Stockham, + sign) and keep the
+//   slab's SW columns;
+//   FFT the slab's columns (occupied rows only are non-zero), per pol;
+//   XX, YY, Re/Im XY of the slab's SW x N pixels are added to registers.
+// The fftshift is folded into the gridding weights, so FFT index k is image
+// index k.  No atomics: reruns are bitwise identical.
+#include <algorithm>
+
 #include "epic_internal.h"
+#include "kcommon.cuh"
 
 namespace epic {
+
+namespace {
+
+constexpr int kFThreads = 256;
+constexpr int kRowChunk = 16;
+
+struct FusedArgs {
+    const uint8_t* volt;
+    int T, C, A, P, N, logN, SW, n_s, nprod;
+    const int4* box;
+    const int* cell_off;
+    const int* cell_ptr;
+    const int* ce;
+    const float2* cw;
+    const float2* twiddle;
+    float* out;
+    int accumulate;
+    int box_x, box_y;  // largest occupied box (for shared-memory carving)
+};
+
+// Shared memory carve-up (float2 units):
+//   tw    [N/2]                      twiddles
+//   vs    [A][P]                     unpacked voltages of the frame
+//   gbuf  [P][16][box_x]             gridded row chunk
+//   fa,fb [max(16 N, SW (N+1))]      FFT ping-pong buffers (rows, then columns)
+//   hbuf  [P][box_y][SW]             slab columns of the row FFTs
+//   ex    [SW][N+1]                  column FFT result of pol X (kept for the products)
+__host__ __device__ inline size_t fused_smem_elems(int N, int A, int P, int SW, int bx, int by)
+{
+    const size_t fft = (size_t)std::max(kRowChunk * N, SW * (N + 1));
+    return (size_t)N / 2 + (size_t)A * P + (size_t)P * kRowChunk * bx + 2 * fft + (size_t)P * by * SW +
+           (P == 2 ? (size_t)SW * (N + 1) : 0);
+}
+
+template <int NPT>  // accumulated pixels per thread (per product)
+__global__ void __launch_bounds__(kFThreads, 1) k_fused_fp32(FusedArgs a)
+{
+    extern __shared__ __align__(16) float2 fsm[];
+    const int N = a.N, P = a.P, A = a.A, SW = a.SW;
+    const int fft = max(kRowChunk * N, SW * (N + 1));
+    float2* tw = fsm;
+    float2* vs = tw + N / 2;
+    float2* gbuf = vs + A * P;
+    float2* fa = gbuf + P * kRowChunk * a.box_x;
+    float2* fb = fa + fft;
+    float2* hbuf = fb + fft;
+    float2* ex = hbuf + P * a.box_y * SW;
+    for (int i = threadIdx.x; i < N / 2; i += blockDim.x) tw[i] = a.twiddle[i];
+
+    const int items = a.C * a.n_s;
+    const int kxl = threadIdx.x % SW;              // slab-local column of this thread
+    const int ky0 = threadIdx.x / SW, kys = kFThreads / SW;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int s = item % a.n_s, c = item / a.n_s;
+        const int4 b = a.box[c];
+        const int x0 = b.x, y0 = b.y, nxp = b.z, nyp = b.w;
+        const int* ptr = a.cell_ptr + a.cell_off[c];
+        float axx[NPT], ayy[NPT], arx[NPT], aix[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+
+        for (int t = 0; t < a.T; ++t) {
+            __syncthreads();
+            const uint8_t* fr = a.volt + ((size_t)t * a.C + c) * (size_t)A * P;
+            for (int i = threadIdx.x; i < A * P; i += blockDim.x) vs[i] = unpack44(fr[i]);
+            __syncthreads();
+            // ---- rows: grid 16-row chunks, FFT along x, keep the slab columns
+            for (int r0 = 0; r0 < nyp; r0 += kRowChunk) {
+                const int nr = min(kRowChunk, nyp - r0);
+                for (int cell = threadIdx.x; cell < nr * nxp; cell += blockDim.x) {
+                    const int r = cell / nxp, x = cell - r * nxp;
+                    const int q0 = ptr[(r0 + r) * nxp + x], q1 = ptr[(r0 + r) * nxp + x + 1];
+                    float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
+                    for (int q = q0; q < q1; ++q) {
+                        const int e = a.ce[q];
+                        const float2 w = a.cw[q];
+                        g0 = cfma(w, vs[e * P], g0);
+                        if (P == 2) g1 = cfma(w, vs[e * P + 1], g1);
+                    }
+                    gbuf[r * nxp + x] = g0;
+                    if (P == 2) gbuf[kRowChunk * nxp + r * nxp + x] = g1;
+                }
+                for (int p = 0; p < P; ++p) {
+                    __syncthreads();
+                    // zero-padded rows of length N with the box at columns x0..x0+nxp
+                    for (int i = threadIdx.x; i < nr * N; i += blockDim.x) {
+                        const int r = i / N, x = i - r * N;
+                        const int xr = x - x0;
+                        fa[i] = (xr >= 0 && xr < nxp) ? gbuf[p * kRowChunk * nxp + r * nxp + xr] : make_float2(0.f, 0.f);
+                    }
+                    float2* res = fft_stockham_r2(fa, fb, a.logN, nr, 1, N, tw);
+                    for (int i = threadIdx.x; i < nr * SW; i += blockDim.x) {
+                        const int r = i / SW, k = i - r * SW;
+                        hbuf[(p * a.box_y + r0 + r) * SW + k] = res[r * N + s * SW + k];
+                    }
+                }
+                __syncthreads();
+            }
+            // ---- columns: FFT along y of the SW slab columns, per pol
+            for (int p = 0; p < P; ++p) {
+                for (int i = threadIdx.x; i < SW * N; i += blockDim.x) {
+                    const int k = i / N, y = i - k * N;
+                    const int yr = y - y0;
+                    fa[k * (N + 1) + y] = (yr >= 0 && yr < nyp) ? hbuf[(p * a.box_y + yr) * SW + k] : make_float2(0.f, 0.f);
+                }
+                float2* res = fft_stockham_r2(fa, fb, a.logN, SW, 1, N + 1, tw);
+                if (p == 0 && P == 2) {
+                    for (int i = threadIdx.x; i < SW * (N + 1); i += blockDim.x) ex[i] = res[i];
+                    __syncthreads();
+                } else {
+                    // ---- products of this thread's pixels (kx = kxl, ky = ky0 + j kys)
+                    const float2* xs = P == 2 ? ex : res;
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) {
+                        const int ky = ky0 + j * kys;
+                        if (ky < N) {
+                            const float2 X = xs[kxl * (N + 1) + ky];
+                            axx[j] = fmaf(X.x, X.x, fmaf(X.y, X.y, axx[j]));
+                            if (P == 2) {
+                                const float2 Y = res[kxl * (N + 1) + ky];
+                                ayy[j] = fmaf(Y.x, Y.x, fmaf(Y.y, Y.y, ayy[j]));
+                                arx[j] = fmaf(X.x, Y.x, fmaf(X.y, Y.y, arx[j]));
+                                aix[j] = fmaf(X.y, Y.x, fmaf(-X.x, Y.y, aix[j]));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // ---- images
+        const int kx = s * SW + kxl;
+        if (kx < N) {
+            const size_t NN = (size_t)N * N;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                const int ky = ky0 + j * kys;
+                if (ky >= N) continue;
+                float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * N + kx;
+                o[0] = (a.accumulate ? o[0] : 0.f) + axx[j];
+                if (a.nprod == 4) {
+                    o[NN] = (a.accumulate ? o[NN] : 0.f) + ayy[j];
+                    o[2 * NN] = (a.accumulate ? o[2 * NN] : 0.f) + arx[j];
+                    o[3 * NN] = (a.accumulate ? o[3 * NN] : 0.f) + aix[j];
+                }
+            }
+        }
+    }
+}
+
+// pixels per thread for a grid size: SW columns x N rows over 256 threads
+int npt_for(int N, int SW) { return std::max(1, SW * N / kFThreads); }
+
+}  // namespace
+
 epic_status fused_setup(epic_plan_s* p)
 {
-    p->last_error = "fused FP32 path not built yet";
-    return EPIC_ERR_UNSUPPORTED;
+    const int N = p->N;
+    const int SW = N >= 256 ? 16 : std::min(32, N);
+    const size_t bytes =
+        sizeof(float2) * fused_smem_elems(N, p->A, p->P, SW, p->box_max_x, p->box_max_y);
+    if ((int)bytes > p->smem_optin) {
+        p->last_error = "fused FP32 path: occupied grid or element count too large for shared memory";
+        return EPIC_ERR_UNSUPPORTED;
+    }
+    p->slab = SW;
+    p->fused_variant = npt_for(N, SW);
+    p->time_chunk = p->max_time;
+    cudaError_t e = cudaSuccess;
+#define EPIC_FUSED_ATTR(n)                                                                                      \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_fp32<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                   p->smem_optin);
+    EPIC_FUSED_ATTR(1)
+    EPIC_FUSED_ATTR(2)
+    EPIC_FUSED_ATTR(4)
+    EPIC_FUSED_ATTR(8)
+    EPIC_FUSED_ATTR(16)
+#undef EPIC_FUSED_ATTR
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_fused_fp32)");
+    return EPIC_OK;
 }
-epic_status fused_run(epic_plan_s*, const uint8_t*, int, cudaStream_t, float*, bool) { return EPIC_ERR_UNSUPPORTED; }
+
+epic_status fused_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate)
+{
+    FusedArgs a{};
+    a.volt = volt;
+    a.T = T;
+    a.C = p->C;
+    a.A = p->A;
+    a.P = p->P;
+    a.N = p->N;
+    a.logN = p->logN;
+    a.SW = p->slab;
+    a.n_s = (p->N + p->slab - 1) / p->slab;
+    a.nprod = p->nprod;
+    a.box = p->dt.box;
+    a.cell_off = p->dt.cell_off;
+    a.cell_ptr = p->dt.cell_ptr;
+    a.ce = p->dt.contrib_e;
+    a.cw = p->dt.contrib_w;
+    a.twiddle = p->dt.twiddle;
+    a.out = out;
+    a.accumulate = accumulate ? 1 : 0;
+    a.box_x = p->box_max_x;
+    a.box_y = p->box_max_y;
+    const size_t bytes = sizeof(float2) * fused_smem_elems(a.N, a.A, a.P, a.SW, a.box_x, a.box_y);
+    const int items = a.C * a.n_s;
+    const int grid = std::min(items, p->sm_count);
+    ev_begin(p, "k_fused_fp32", s);
+    switch (p->fused_variant) {
+        case 1: k_fused_fp32<1><<<grid, kFThreads, bytes, s>>>(a); break;
+        case 2: k_fused_fp32<2><<<grid, kFThreads, bytes, s>>>(a); break;
+        case 4: k_fused_fp32<4><<<grid, kFThreads, bytes, s>>>(a); break;
+        case 8: k_fused_fp32<8><<<grid, kFThreads, bytes, s>>>(a); break;
+        default: k_fused_fp32<16><<<grid, kFThreads, bytes, s>>>(a); break;
+    }
+    ev_end(p, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, "fused FP32 launch");
+    return EPIC_OK;
+}
+
 }  // namespace epic

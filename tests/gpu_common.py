@@ -7,7 +7,7 @@ import oracle
 # channel and per product (XX, YY, Re XY, Im XY).  FP32 paths: 1e-5; the FP16
 # tensor-core DFT-as-GEMM path: 2e-3 of the image peak.
 TOL = {"plain": 1e-5, "fused": 1e-5, "dftgemm": 2e-3}
-GPU_PATHS = ["plain", "dftgemm"]
+GPU_PATHS = ["plain", "fused", "dftgemm"]
 
 
 def rel_errors(gpu: np.ndarray, ref: np.ndarray):
