@@ -171,6 +171,47 @@ const char* epic_last_error(epic_plan_t plan);
  * device; returns EPIC_ERR_CUDA without a usable device. */
 epic_status epic_device_query(int* sm_count, int* smem_optin_bytes, int* cc_major, int* cc_minor);
 
+/* ---------------------------------------------------------------------------
+ * Streaming server (continuous batching).  Voltage blocks from several stations
+ * (one plan per station type) are admitted as they arrive and imaged
+ * concurrently: each block waits until one of max_slots CUDA streams is free,
+ * a range of the server's device pool (max_device_bytes, allocated once at
+ * creation) holds it, and its plan is idle -- blocks of one plan run one at a
+ * time in submission order, blocks of different plans overlap on the device.
+ * Images go to caller-owned device accumulators (use EPIC_ACCUMULATE to continue
+ * an integration across blocks).  Latency of a block = wall time from submission
+ * to completion of its kernels.  A plan given to a server must not be used by
+ * other epic_image calls until its blocks are done.
+ * ------------------------------------------------------------------------- */
+typedef struct epic_server_s* epic_server_t;
+
+/* max_slots in 1..64; max_device_bytes >= 256.  EPIC_ERR_OOM if the pool cannot
+ * be allocated. */
+epic_status epic_server_create(size_t max_device_bytes, int max_slots, epic_server_t* out);
+
+/* Queue one block: volt_host = host uint8[T][C][A][P] of `plan` (must stay valid and
+ * unchanged until the ticket completes), out_dev = device images of the plan's
+ * shape, flags EPIC_RESET or EPIC_ACCUMULATE.  Returns at once with a ticket;
+ * EPIC_ERR_BUSY when the admission queue (4 x max_slots blocks) is full,
+ * EPIC_ERR_OOM when the block can never fit the pool. */
+epic_status epic_server_submit(epic_server_t server, epic_plan_t plan, const uint8_t* volt_host, int T,
+                               float* out_dev, unsigned flags, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the block's images are complete (then returns the
+ * block's status and its latency in ms). */
+epic_status epic_server_poll(epic_server_t server, uint64_t ticket, int* done, double* latency_ms);
+
+/* Block up to timeout_ms for a ticket, then release it (EPIC_ERR_TIMEOUT if not done;
+ * EPIC_ERR_NOT_FOUND for an unknown or already released ticket). */
+epic_status epic_server_wait(epic_server_t server, uint64_t ticket, int timeout_ms, double* latency_ms);
+
+/* Completed blocks so far, p50 / p99 of their latencies (ms; -1 when none), blocks
+ * on the device now. */
+epic_status epic_server_stats(epic_server_t server, int* completed, double* p50_ms, double* p99_ms, int* in_flight);
+
+/* Stop admitting, finish blocks already on the device, free everything. NULL is OK. */
+epic_status epic_server_destroy(epic_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

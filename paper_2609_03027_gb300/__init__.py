@@ -6,6 +6,6 @@ sm_103a kernels of libepic.so; this package only builds and calls it.
 """
 from .epic import (  # noqa: F401
     ACCUMULATE, EXPORTED, PATHS, PATH_AUTO, PATH_DFTGEMM_FP16, PATH_FUSED_FP32, PATH_PLAIN_FP32, RESET,
-    EpicError, Plan, device_query, library_path, load,
+    EpicError, Plan, Server, device_query, library_path, load,
 )
 from .buildlib import build  # noqa: F401

@@ -37,7 +37,8 @@ STATUS = {0: "EPIC_OK", 1: "EPIC_ERR_INVALID_ARG", 2: "EPIC_ERR_GRID_OVERFLOW", 
 # Every symbol declared in include/epic.h (checked by the ABI tests).
 EXPORTED = ["epic_plan_create", "epic_plan_destroy", "epic_image", "epic_image_host", "epic_sync",
             "epic_kernel_times", "epic_plan_get_info", "epic_status_str", "epic_last_error",
-            "epic_device_query"]
+            "epic_device_query", "epic_server_create", "epic_server_submit", "epic_server_poll",
+            "epic_server_wait", "epic_server_stats", "epic_server_destroy"]
 
 
 class EpicError(RuntimeError):
@@ -100,6 +101,12 @@ def load(build_if_missing: bool = True):
         L.epic_last_error.argtypes = [vp]
         L.epic_last_error.restype = ctypes.c_char_p
         L.epic_device_query.argtypes = [P(i), P(i), P(i), P(i)]
+        L.epic_server_create.argtypes = [ctypes.c_size_t, i, P(vp)]
+        L.epic_server_submit.argtypes = [vp, vp, vp, i, vp, u, P(ctypes.c_uint64)]
+        L.epic_server_poll.argtypes = [vp, ctypes.c_uint64, P(i), P(ctypes.c_double)]
+        L.epic_server_wait.argtypes = [vp, ctypes.c_uint64, i, P(ctypes.c_double)]
+        L.epic_server_stats.argtypes = [vp, P(i), P(ctypes.c_double), P(ctypes.c_double), P(i)]
+        L.epic_server_destroy.argtypes = [vp]
         for name in EXPORTED:
             if name not in ("epic_status_str", "epic_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -245,6 +252,73 @@ class Plan:
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.epic_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over the C ABI (epic_server_*).
+
+    Blocks of different plans run concurrently on ``slots`` streams; blocks are
+    admitted by queue length and a device pool of ``device_bytes``.  Host blocks
+    passed to submit() are kept referenced until their ticket is waited for.
+    """
+
+    def __init__(self, device_bytes: int, slots: int = 4):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.epic_server_create(int(device_bytes), int(slots), ctypes.byref(h)))
+        self._h = h
+        self._keep: Dict[int, object] = {}
+
+    def submit(self, plan: "Plan", volt: np.ndarray, out, accumulate: bool = False) -> Optional[int]:
+        """Queue a host block; returns a ticket, or None when the server is busy."""
+        v = np.ascontiguousarray(volt, dtype=np.uint8)
+        if v.ndim != 4 or v.shape[1:] != (plan.n_chan, plan.n_ant, plan.n_pol):
+            raise ValueError("block must be uint8 [T][C][A][P] of the plan")
+        t = ctypes.c_uint64()
+        st = self._lib.epic_server_submit(self._h, plan._handle(), v.ctypes.data if v.shape[0] else None,
+                                          int(v.shape[0]), out.data_ptr(), ACCUMULATE if accumulate else RESET,
+                                          ctypes.byref(t))
+        if st == 4:  # EPIC_ERR_BUSY
+            return None
+        _check(self._lib, st)
+        self._keep[t.value] = (v, out)
+        return int(t.value)
+
+    def poll(self, ticket: int) -> Tuple[bool, float]:
+        d, lat = ctypes.c_int(), ctypes.c_double()
+        _check(self._lib, self._lib.epic_server_poll(self._h, ticket, ctypes.byref(d), ctypes.byref(lat)))
+        return bool(d.value), float(lat.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> float:
+        lat = ctypes.c_double()
+        st = self._lib.epic_server_wait(self._h, ticket, int(timeout_ms), ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        _check(self._lib, st)
+        return float(lat.value)
+
+    def stats(self) -> Dict[str, float]:
+        n, p50, p99, fl = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(self._lib, self._lib.epic_server_stats(self._h, ctypes.byref(n), ctypes.byref(p50), ctypes.byref(p99),
+                                                      ctypes.byref(fl)))
+        return {"completed": n.value, "p50_ms": p50.value, "p99_ms": p99.value, "in_flight": fl.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.epic_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __enter__(self):
         return self

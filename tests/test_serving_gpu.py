@@ -1,0 +1,107 @@
+"""Streaming server (continuous batching): every block's images are the same when
+imaged alone and in the mix, integrations continue across blocks, and latency
+statistics are reported."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import epic_synth as synth
+
+torch = pytest.importorskip("torch")
+
+import paper_2609_03027_gb300 as E  # noqa: E402
+
+
+def _stations():
+    # four station types of different sizes, each with its own plan and path
+    specs = [
+        dict(n_ant=24, n_chan=3, n_pol=2, grid_n=32, gcf_k=3, n_time=9, seed=61, diameter_m=9.0),
+        dict(n_ant=64, n_chan=2, n_pol=2, grid_n=64, gcf_k=5, n_time=20, seed=62, diameter_m=16.0),
+        dict(n_ant=120, n_chan=4, n_pol=2, grid_n=64, gcf_k=3, n_time=12, seed=63, diameter_m=17.0),
+        dict(n_ant=40, n_chan=2, n_pol=1, grid_n=32, gcf_k=3, n_time=7, seed=64, diameter_m=9.0),
+    ]
+    paths = ["dftgemm", "fused", "dftgemm", "plain"]
+    return [(synth.small_config(**sp), path) for sp, path in zip(specs, paths)]
+
+
+@pytest.mark.gpu
+def test_each_block_same_alone_and_in_the_mix():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    stations = _stations()
+    plans = [E.Plan.from_config(cfg, path=path) for cfg, path in stations]
+    blocks = []
+    for si, (cfg, _) in enumerate(stations):
+        for b in range(3):
+            T = cfg.n_time - b
+            v = synth.make_voltages(cfg, t0=5 * b, n_time=T)
+            blocks.append((si, v))
+    # alone
+    alone = []
+    for si, v in blocks:
+        out = plans[si].image(torch.from_numpy(v).cuda())
+        torch.cuda.synchronize()
+        alone.append(out.cpu().numpy())
+    # in the mix: all submitted at once, different stations overlap on the device
+    outs = [torch.full((stations[si][0].n_chan, stations[si][0].n_prod, stations[si][0].grid_n,
+                        stations[si][0].grid_n), -1.0, device="cuda") for si, _ in blocks]
+    with E.Server(device_bytes=64 << 20, slots=4) as srv:
+        tickets = []
+        for (si, v), o in zip(blocks, outs):
+            t = None
+            while t is None:
+                t = srv.submit(plans[si], v, o)
+            tickets.append(t)
+        lat = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(blocks)
+    assert all(x > 0 for x in lat)
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    for (si, v), o, ref in zip(blocks, outs, alone):
+        assert np.array_equal(o.cpu().numpy(), ref), f"station {si}"
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.gpu
+def test_integration_continues_across_blocks():
+    cfg, path = _stations()[1]
+    plan = E.Plan.from_config(cfg, path="dftgemm")
+    vs = [synth.make_voltages(cfg, t0=7 * b, n_time=cfg.n_time) for b in range(3)]
+    ref = torch.empty((cfg.n_chan, 4, cfg.grid_n, cfg.grid_n), device="cuda")
+    for b, v in enumerate(vs):
+        plan.image(torch.from_numpy(v).cuda(), out=ref, accumulate=b > 0)
+    acc = torch.full_like(ref, 5.0)
+    with E.Server(device_bytes=32 << 20, slots=2) as srv:
+        ts = [srv.submit(plan, v, acc, accumulate=b > 0) for b, v in enumerate(vs)]
+        for t in ts:
+            srv.wait(t)
+    assert torch.equal(acc, ref)
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_block_larger_than_pool_is_refused():
+    cfg, _ = _stations()[0]
+    plan = E.Plan.from_config(cfg, path="plain")
+    v = synth.make_voltages(cfg)
+    out = torch.empty((cfg.n_chan, 4, cfg.grid_n, cfg.grid_n), device="cuda")
+    with E.Server(device_bytes=1024, slots=1) as srv:
+        with pytest.raises(E.EpicError, match="OOM"):
+            srv.submit(plan, v, out)
+    plan.close()
+
+
+def test_server_argument_checks_on_host():
+    L = E.load()
+    h = ctypes.c_void_p()
+    assert L.epic_server_create(1 << 20, 0, ctypes.byref(h)) == 1      # no slots
+    assert L.epic_server_create(1 << 20, 65, ctypes.byref(h)) == 1     # too many slots
+    assert L.epic_server_create(16, 2, ctypes.byref(h)) == 1           # pool too small
+    assert L.epic_server_create(1 << 20, 2, None) == 1
+    t = ctypes.c_uint64()
+    assert L.epic_server_submit(None, None, None, 0, None, 0, ctypes.byref(t)) == 1
+    d, lat = ctypes.c_int(), ctypes.c_double()
+    assert L.epic_server_poll(None, 1, ctypes.byref(d), ctypes.byref(lat)) == 1
+    assert L.epic_server_destroy(None) == 0
