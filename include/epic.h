@@ -171,6 +171,25 @@ const char* epic_last_error(epic_plan_t plan);
  * device; returns EPIC_ERR_CUDA without a usable device. */
 epic_status epic_device_query(int* sm_count, int* smem_optin_bytes, int* cc_major, int* cc_minor);
 
+/* Same result as epic_image, but the call allocates no device memory and uses no
+ * plan scratch: its grid scratch is a fixed 32 MiB array in the library's device
+ * image (held by every GPU that loads the library until the process exits).  For
+ * callers that may not call cudaMalloc while imaging -- e.g. code running inside
+ * a framework that owns the device memory through its own pool, or real-time
+ * loops where an allocation could stall the device.  The paper has no
+ * counterpart; it runs the plain FP32 pipeline (grid, row FFT, column FFT,
+ * products) in time chunks that fit the array, with any plan.
+ * - EPIC_ERR_UNSUPPORTED (with the sizes in epic_last_error) when one time sample
+ *   of the plan needs more than 32 MiB of grids (n_chan x n_pol x N^2 x 8 bytes).
+ * - The first call on a device looks up the array's device address and sets the
+ *   kernels' shared-memory limits there; make that first call before any stream
+ *   capture.
+ * - All calls share the array (it keeps the last call's contents; each call writes
+ *   every byte it reads first): calls that overlap on the GPU race on it.
+ * flags: EPIC_RESET or EPIC_ACCUMULATE.  Stream-ordered, asynchronous. */
+epic_status epic_image_static_scratch(epic_plan_t plan, const uint8_t* volt, int T, void* cuda_stream, float* out,
+                                      unsigned flags);
+
 /* ---------------------------------------------------------------------------
  * Streaming server (continuous batching).  Voltage blocks from several stations
  * (one plan per station type) are admitted as they arrive and imaged
