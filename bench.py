@@ -236,18 +236,21 @@ def recorded_traffic(kernel: str, workload: int):
     return float(rec["bytes_per_launch"])
 
 
-def run_e2e(E, cfg, volt, out, T, units, world, dev, args):
+def run_e2e(E, cfg, volt, out, T, units, world, dev, args, tuning=None):
     """Same metric through the host-buffer call: pinned H2D + imaging + D2H every step."""
     import torch
     plan = E.Plan.from_config(cfg, path=args.path, max_time=T)
+    for name, val in (tuning or {}).items():       # the values the autotuner chose for the device run
+        plan.set_param(name, val)
+    graph = not args.no_graph
     h_volt = torch.from_numpy(volt).pin_memory()
     h_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
     for _ in range(2):
-        plan.image_host_ptr(h_volt.data_ptr(), T, h_out.data_ptr())
+        plan.image_host_ptr(h_volt.data_ptr(), T, h_out.data_ptr(), graph=graph)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        plan.image_host_ptr(h_volt.data_ptr(), T, h_out.data_ptr())
+        plan.image_host_ptr(h_volt.data_ptr(), T, h_out.data_ptr(), graph=graph)
     e2e_s = reduce_max((time.perf_counter() - t0) / args.e2e_steps, world, dev)
     plan.close()
     return {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(volt.nbytes),
@@ -269,6 +272,8 @@ def main():
     ap.add_argument("--ref-time", type=int, default=250, help="time samples per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time", type=int, default=0, help="override the block length T (small profiling cases)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (plan defaults)")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -294,11 +299,16 @@ def main():
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    use_graph = not args.no_graph
+
     def time_path(path, steps, warmup, sample_clocks=False):
         plan = E.Plan.from_config(cfg, path=path, max_time=T)
+        tuning = None if args.no_tune else plan.tune(d_volt, out=out, reps=2)
         info = plan.info()
+        if tuning is not None:
+            info["tuning"] = tuning["params"]
         for _ in range(warmup):
-            plan.image(d_volt, out=out)
+            plan.image(d_volt, out=out, graph=use_graph, time_kernels=True)
         torch.cuda.synchronize()
         barrier(world)
         torch.cuda.synchronize()
@@ -312,7 +322,7 @@ def main():
         for i in range(steps):
             flush.fill_(i & 0xFF)                       # evict the previous step's data from L2
             starts[i].record(stream)
-            plan.image(d_volt, out=out, time_kernels=True)
+            plan.image(d_volt, out=out, time_kernels=True, graph=use_graph)
             stops[i].record(stream)
             kt = plan.kernel_times()                   # events on the launching stream
             launches += len(kt)
@@ -365,7 +375,7 @@ def main():
     # end to end through the public host-buffer call: pinned H2D + imaging + D2H each step
     e2e = None
     if args.e2e_steps > 0:
-        e2e = run_e2e(E, cfg, volt, out, T, units, world, dev, args)
+        e2e = run_e2e(E, cfg, volt, out, T, units, world, dev, args, info.get("tuning"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -378,7 +388,9 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config], "path": info.get("path_name", args.path),
                            "global_batch_pixel_updates": units * world, "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "launch": "cuda-graph" if use_graph else "per-kernel",
+                           "tuning": info.get("tuning")},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
                 "cpu_baseline": cpu, "compare": compare}
         print(json.dumps(line), flush=True)

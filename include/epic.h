@@ -124,6 +124,7 @@ typedef struct {
 #define EPIC_RESET       0u /* out = images of this block                                         */
 #define EPIC_ACCUMULATE  1u /* out += images of this block (continue an integration / resume)     */
 #define EPIC_TIME_KERNELS 2u /* record CUDA events around each kernel (see epic_kernel_times)     */
+#define EPIC_GRAPH       4u /* replay the call's kernel sequence as one CUDA graph (see epic_image) */
 
 /* Build a plan: geometry and GCF taps in FP64 on the host (Eq. 1 bracket), the
  * inverse cell -> (element, weight) lists, transform tables, device uploads.
@@ -141,7 +142,12 @@ epic_status epic_plan_destroy(epic_plan_t plan);
  * [C][n_prod][N][N], written (EPIC_RESET) or added to (EPIC_ACCUMULATE).
  * 0 <= T <= max_time; T = 0 with EPIC_RESET zeroes out.  Asynchronous: returns
  * after launching.  The plan's scratch is reused by every call, so calls on one
- * plan must not overlap on different streams. */
+ * plan must not overlap on different streams.
+ * EPIC_GRAPH: the plan records the call's launches (for these volt, out, T and
+ * flags) on a stream of its own into a CUDA graph and launches that graph on
+ * `stream`; later calls with the same arguments only launch the graph again
+ * (one launch per call instead of one per kernel), a call with other arguments
+ * records again and updates the graph in place.  Same images as without the flag. */
 epic_status epic_image(epic_plan_t plan, const uint8_t* volt, int T, void* stream, float* out,
                        unsigned flags);
 
@@ -161,6 +167,39 @@ epic_status epic_sync(epic_plan_t plan);
 epic_status epic_kernel_times(epic_plan_t plan, const char** names, float* ms, int max, int* n_out);
 
 epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
+
+/* Autotuner: times epic_image on the caller's block (device volt, T samples, out
+ * as in epic_image; out is overwritten) for the candidate values of each of the
+ * plan's tuning parameters in turn, keeping the fastest value of each, and leaves
+ * the plan configured with them.  Parameters by path:
+ *   PLAIN_FP32    chunk_mb     grid-buffer budget of one time chunk (MiB)
+ *   FUSED_FP32    slab         image columns per work item
+ *   DFTGEMM_FP16  grid_frames  frames per pass of the gridding kernel;
+ *                 chunk_mb     tile-buffer budget of one (channel group, time chunk)
+ * Images after tuning equal those before up to FP32 rounding order.  reps calls
+ * are timed per candidate (1..100) after one untimed call.  May reallocate the
+ * plan's scratch (EPIC_ERR_OOM if that fails; the plan then keeps working with
+ * its previous values).  Synchronous.  The paper has no counterpart: this picks
+ * the implementation's tiling for the GPU it runs on. */
+typedef struct {
+    int n_timed;            /* candidate configurations timed                                      */
+    float default_ms;       /* one call with the configuration the plan had before                 */
+    float best_ms;          /* one call with the chosen configuration                              */
+    int n_params;           /* entries of names / values                                           */
+    const char* names[8];   /* static parameter names                                              */
+    int values[8];          /* chosen values                                                       */
+} epic_tune_report;
+epic_status epic_plan_tune(epic_plan_t plan, const uint8_t* volt, int T, void* stream, float* out, int reps,
+                           epic_tune_report* report);
+
+/* Set / read one tuning parameter by the names above (e.g. to apply values an
+ * earlier epic_plan_tune reported).  EPIC_ERR_NOT_FOUND: no such parameter on
+ * this plan's path; EPIC_ERR_UNSUPPORTED: the value is not possible for this
+ * plan (the plan is unchanged); EPIC_ERR_OOM when a larger scratch cannot be
+ * allocated.  Images change at most by FP32 rounding order.  Not during a call
+ * in flight on another stream.  The paper has no counterpart. */
+epic_status epic_plan_set_param(epic_plan_t plan, const char* name, int value);
+epic_status epic_plan_get_param(epic_plan_t plan, const char* name, int* value);
 
 /* Static text of a status code, and the detail of the last error on a plan
  * (or of the last failed epic_plan_create when plan is NULL).  Never NULL. */

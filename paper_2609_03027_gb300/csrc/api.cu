@@ -63,6 +63,8 @@ void free_plan(epic_plan_s* p)
         cudaEventDestroy(ev.start);
         cudaEventDestroy(ev.stop);
     }
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     cudaSetDevice(cur);
     delete p;
 }
@@ -91,13 +93,15 @@ void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s)
         p->events.push_back(ev);
     }
     p->events[p->n_events].name = name;
-    cudaEventRecord(p->events[p->n_events].start, s);
+    if (p->capturing) cudaEventRecordWithFlags(p->events[p->n_events].start, s, cudaEventRecordExternal);
+    else cudaEventRecord(p->events[p->n_events].start, s);
 }
 
 void ev_end(epic_plan_s* p, cudaStream_t s)
 {
     if (!p->timing || p->n_events >= p->events.size()) return;
-    cudaEventRecord(p->events[p->n_events].stop, s);
+    if (p->capturing) cudaEventRecordWithFlags(p->events[p->n_events].stop, s, cudaEventRecordExternal);
+    else cudaEventRecord(p->events[p->n_events].stop, s);
     ++p->n_events;
 }
 
@@ -322,7 +326,10 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
     return EPIC_OK;
 }
 
-static epic_status image_impl(epic_plan_t p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
+}  // extern "C"
+
+namespace epic {
+epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
 {
     const bool acc = (flags & EPIC_ACCUMULATE) != 0;
     p->timing = (flags & EPIC_TIME_KERNELS) != 0;
@@ -342,6 +349,86 @@ static epic_status image_impl(epic_plan_t p, const uint8_t* volt, int T, cudaStr
     }
     return EPIC_ERR_INVALID_ARG;
 }
+}  // namespace epic
+
+extern "C" {
+
+// Timing events the recorded graph will need (created before recording).
+static void reserve_events(epic_plan_t p, int T)
+{
+    size_t n = 8;
+    const int chunks = p->time_chunk > 0 ? (T + p->time_chunk - 1) / p->time_chunk : 1;
+    if (p->path == EPIC_PATH_PLAIN_FP32) n = 4ull * chunks;
+    else if (p->path == EPIC_PATH_DFTGEMM_FP16) n = 2ull * chunks * ((p->C + p->tc.cg - 1) / std::max(1, p->tc.cg));
+    n = std::min<size_t>(n + 2, 8192);
+    while (p->events.size() < n) {
+        epic::KernelEvent ev{"", nullptr, nullptr};
+        if (cudaEventCreate(&ev.start) != cudaSuccess) break;
+        if (cudaEventCreate(&ev.stop) != cudaSuccess) {
+            cudaEventDestroy(ev.start);
+            break;
+        }
+        p->events.push_back(ev);
+    }
+}
+
+// EPIC_GRAPH: launch the recorded graph, recording (or re-recording) it first
+// when the arguments differ from the ones it was recorded for.
+static epic_status image_graph(epic_plan_t p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
+{
+    const unsigned f = flags & ~EPIC_GRAPH;
+    p->timing = (f & EPIC_TIME_KERNELS) != 0;
+    if (!(p->gexec && p->g_volt == volt && p->g_out == out && p->g_T == T && p->g_flags == f)) {
+        if (!p->cap_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaStreamCreateWithFlags(graph recording)");
+        }
+        if (p->timing) reserve_events(p, T);
+        cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaStreamBeginCapture");
+        p->capturing = true;
+        epic_status st = epic::image_run(p, volt, T, p->cap_stream, out, f);
+        p->capturing = false;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (st != EPIC_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != EPIC_OK ? st : epic::cuda_fail(p, e, "cudaStreamEndCapture");
+        }
+        if (p->gexec) {
+            cudaGraphExecUpdateResultInfo info{};
+            if (cudaGraphExecUpdate(p->gexec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+        }
+        if (!p->gexec) e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            p->g_T = -1;
+            return epic::cuda_fail(p, e, "cudaGraphInstantiate");
+        }
+        p->g_volt = volt;
+        p->g_out = out;
+        p->g_T = T;
+        p->g_flags = f;
+        p->g_events = p->n_events;
+    }
+    p->n_events = p->g_events;
+    p->last_stream = s;
+    cudaError_t e = cudaGraphLaunch(p->gexec, s);
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaGraphLaunch");
+    return EPIC_OK;
+}
+
+static epic_status image_impl(epic_plan_t p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
+{
+    if ((flags & EPIC_GRAPH) && T > 0) return image_graph(p, volt, T, s, out, flags);
+    return epic::image_run(p, volt, T, s, out, flags & ~EPIC_GRAPH);
+}
 
 epic_status epic_image(epic_plan_t p, const uint8_t* volt, int T, void* stream, float* out, unsigned flags)
 {
@@ -354,7 +441,7 @@ epic_status epic_image(epic_plan_t p, const uint8_t* volt, int T, void* stream, 
         p->last_error = "NULL voltage or image pointer";
         return EPIC_ERR_INVALID_ARG;
     }
-    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)) {
+    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS | EPIC_GRAPH)) {
         p->last_error = "unknown flag bits";
         return EPIC_ERR_INVALID_ARG;
     }
@@ -379,7 +466,7 @@ epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void
         p->last_error = "bad T or NULL host pointer";
         return EPIC_ERR_INVALID_ARG;
     }
-    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)) {
+    if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS | EPIC_GRAPH)) {
         p->last_error = "unknown flag bits";
         return EPIC_ERR_INVALID_ARG;
     }

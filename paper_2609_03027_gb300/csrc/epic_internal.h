@@ -48,6 +48,11 @@ struct TcState {
     int grid_smem = 0;             // dynamic shared memory of the gridding kernel
     bool grid_csr_smem = false;    // gridding kernel stages the cell lists in shared memory
     int grid_frames = 1;           // frames gridded per pass by the gridding kernel
+    bool grid_ps = false;          // persistent gridding kernel (cell lists staged per channel)
+    bool grid_cplx = false;        // complex GCF weights (table GCF)
+    int grid_blocks = 0;           // blocks of the persistent gridding kernel
+    int grid_max_cells = 0;        // largest occupied box (cells)
+    int grid_max_list = 0;         // (cell, element) entries per channel
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2
     uint32_t* a2w = nullptr;       // stage-2 operand rows as packed FP16 pairs (fast variant)
     long long* a2w_off = nullptr;
@@ -98,12 +103,24 @@ struct epic_plan_s {
     int fused_variant = 0;                // kernel variant chosen for fused paths
     int slab = 0;                         // output columns per work item (fused paths)
 
+    size_t chunk_budget = 0;              // scratch budget of one time chunk (chunked paths)
+
     // errors / timing
     std::string last_error;
     cudaStream_t last_stream = nullptr;
     bool timing = false;
     std::vector<epic::KernelEvent> events;
     size_t n_events = 0;
+
+    // CUDA-graph replay (EPIC_GRAPH)
+    cudaStream_t cap_stream = nullptr;    // plan-owned stream the launches are recorded on
+    bool capturing = false;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_volt = nullptr;         // arguments the graph was recorded for
+    const float* g_out = nullptr;
+    int g_T = -1;
+    unsigned g_flags = 0;
+    size_t g_events = 0;                  // timing events recorded in the graph
 };
 
 namespace epic {
@@ -118,17 +135,23 @@ void build_twiddles(int N, std::vector<float2>& tw);
 void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s);
 void ev_end(epic_plan_s* p, cudaStream_t s);
 epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);
+// one epic_image call after argument checks (flags without EPIC_GRAPH handling)
+epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags);
 
 // k_plain.cu
 epic_status plain_setup(epic_plan_s* p);
 epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+epic_status plain_set_chunk(epic_plan_s* p, size_t budget);
 
 // k_fused.cu
 epic_status fused_setup(epic_plan_s* p);
 epic_status fused_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+epic_status fused_set_slab(epic_plan_s* p, int SW);
 
 // k_dftgemm.cu
 epic_status dftgemm_setup(epic_plan_s* p);
 epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+epic_status dftgemm_grid_config(epic_plan_s* p, int F);
+epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
 
 }  // namespace epic

@@ -264,6 +264,205 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
     }
 }
 
+// Persistent gridding kernel: block b owns the contiguous range [w0, w1) of the
+// chunk's (channel, frame) pairs in channel-major order, so every block grids the
+// same number of frames (+-1) and stages the cell lists of at most a few channels.
+// Frames go in passes of up to F frames of one channel; the raw voltage bytes of
+// the next pass are fetched by the TMA engine (one bulk copy per frame) while the
+// current pass is gridded.  Each thread owns two horizontally adjacent cells per
+// task, walks their (element, weight) lists once per pass and applies every entry
+// to the pass's frames, then writes FP16 pairs into the swizzled UMMA tiles as the
+// gather kernel above does.  CPLX selects complex weights (table GCF).
+struct GridArgs {
+    const uint8_t* volt;
+    int t0, c0, n_ch, nt, C, A, P;
+    const int4* box;
+    const int* cell_off;
+    const int* cell_ptr;
+    const int* ce;
+    const float2* cw;
+    uint8_t* tiles;
+    unsigned long long tile_stride;
+    int* status;
+    int max_cells;  // largest nx * ny over the channels
+    int max_list;   // largest number of (cell, element) entries of a channel
+    int bulk;       // 1: voltage frames copied by the TMA engine (A*P % 16 == 0, 16-byte aligned base)
+};
+
+__host__ __device__ inline size_t grid_ps_smem(int F, int A, int P, int max_cells, int max_list, bool cplx)
+{
+    const size_t ap = (size_t)((A * P + 15) & ~15);
+    size_t b = 2ull * F * ap + 16ull * F * A + 4ull * ((max_cells + 2) & ~1);
+    b += cplx ? 4ull * ((max_list + 1) & ~1) + 8ull * max_list : 8ull * max_list;
+    return b;
+}
+
+template <bool CPLX, int F>
+__global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
+{
+    extern __shared__ __align__(16) uint8_t gsm[];
+    __shared__ uint64_t bar_raw[2];
+    const int tid = threadIdx.x;
+    const int A = a.A, P = a.P, AP = A * P;
+    const int APr = (AP + 15) & ~15;
+    uint8_t* raw = gsm;                                                  // [2][F][APr]
+    float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);           // [F][A]
+    int* sptr = reinterpret_cast<int*>(sv + F * A);                      // [ncell + 1], relative
+    int2* con = reinterpret_cast<int2*>(sptr + ((a.max_cells + 2) & ~1));  // real: (e, w)
+    int* cone = reinterpret_cast<int*>(con);                             // complex: e ...
+    float2* conw = reinterpret_cast<float2*>(cone + ((a.max_list + 1) & ~1));  // ... and w
+
+    const long long W = (long long)a.n_ch * a.nt;
+    const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+    if (tid == 0) {
+        tc::mbar_init(&bar_raw[0], 1);
+        tc::mbar_init(&bar_raw[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (w0 >= w1) return;
+
+    auto pass_len = [&](long long w) {
+        const int f = (int)(w % a.nt);
+        return (int)min((long long)min(F, a.nt - f), w1 - w);
+    };
+    auto fetch = [&](long long w, int b) {  // thread 0: raw bytes of the pass starting at w -> buffer b
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        tc::mbar_expect_tx(&bar_raw[b], (uint32_t)(nf * AP));
+        for (int i = 0; i < nf; ++i)
+            tc::bulk_g2s(raw + (size_t)(b * F + i) * APr,
+                         a.volt + ((size_t)(a.t0 + f + i) * a.C + a.c0 + cl) * (size_t)AP, (uint32_t)AP, &bar_raw[b]);
+    };
+
+    uint32_t ph = 0;          // parity bit per raw buffer
+    uint32_t pending = 0;     // bit b: a bulk copy into raw buffer b is in flight (thread 0)
+    int staged = -1, buf = 0;
+    bool ok = true;
+    if (a.bulk && tid == 0) {
+        fetch(w0, 0);
+        pending = 1u;
+    }
+    for (long long w = w0; w < w1;) {
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        const long long wn = w + nf;
+        const int c = a.c0 + cl;
+        const int4 b = a.box[c];
+        const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
+        if (a.bulk && tid == 0 && wn < w1) {  // the other buffer was consumed by the previous pass
+            fetch(wn, buf ^ 1);
+            pending |= 1u << (buf ^ 1);
+        }
+        if (cl != staged) {  // cell lists of channel c -> shared memory
+            const int* gptr = a.cell_ptr + a.cell_off[c];
+            const int base = gptr[0];
+            const int ncon = gptr[ncell] - base;
+            for (int i = tid; i <= ncell; i += blockDim.x) sptr[i] = gptr[i] - base;
+            for (int i = tid; i < ncon; i += blockDim.x) {
+                if (CPLX) {
+                    cone[i] = a.ce[base + i];
+                    conw[i] = a.cw[base + i];
+                } else {
+                    con[i] = make_int2(a.ce[base + i], __float_as_int(a.cw[base + i].x));
+                }
+            }
+            staged = cl;
+        }
+        // unpack the pass's voltages: (re X, im X, re Y, im Y) per element and frame
+        if (a.bulk) {
+            const bool got = tc::mbar_wait(&bar_raw[buf], (ph >> buf) & 1u, kWaitBudget);
+            if (got) {
+                ph ^= 1u << buf;
+                pending &= ~(1u << buf);
+            }
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+            for (int i = tid; i < nf * A; i += blockDim.x) {
+                const int fi = i / A, e = i - fi * A;
+                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr + (size_t)e * P;
+                const float2 x = unpack44(fr[0]);
+                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+            }
+        } else {
+            for (int i = tid; i < nf * A; i += blockDim.x) {
+                const int fi = i / A, e = i - fi * A;
+                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP + (size_t)e * P;
+                const float2 x = unpack44(fr[0]);
+                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+            }
+        }
+        __syncthreads();
+        const int half = nxp >> 1;
+        const int tasks = nyp * half;
+        for (int task = tid; task < tasks; task += blockDim.x) {
+            const int y = task / half, x = 2 * (task - y * half);
+            float4 g[2][F];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) g[j][fi] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const int r = y * nxp + x + j;
+                const int q1 = sptr[r + 1];
+                for (int q = sptr[r]; q < q1; ++q) {
+                    int e;
+                    float2 wv;
+                    if (CPLX) {
+                        e = cone[q];
+                        wv = conw[q];
+                    } else {
+                        const int2 cr = con[q];
+                        e = cr.x;
+                        wv = make_float2(__int_as_float(cr.y), 0.f);
+                    }
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) {
+                        if (fi < nf) {
+                            const float4 v = sv[fi * A + e];
+                            if (!CPLX) {
+                                g[j][fi].x = fmaf(wv.x, v.x, g[j][fi].x);
+                                g[j][fi].y = fmaf(wv.x, v.y, g[j][fi].y);
+                                g[j][fi].z = fmaf(wv.x, v.z, g[j][fi].z);
+                                g[j][fi].w = fmaf(wv.x, v.w, g[j][fi].w);
+                            } else {
+                                const float2 gx = cfma(wv, make_float2(v.x, v.y), make_float2(g[j][fi].x, g[j][fi].y));
+                                const float2 gy = cfma(wv, make_float2(v.z, v.w), make_float2(g[j][fi].z, g[j][fi].w));
+                                g[j][fi] = make_float4(gx.x, gx.y, gy.x, gy.y);
+                            }
+                        }
+                    }
+                }
+            }
+            const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
+#pragma unroll
+            for (int fi = 0; fi < F; ++fi) {
+                if (fi >= nf) break;
+                uint8_t* tile = a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride;
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(y, kc_re, N1) + within) = pack_h2(g[0][fi].x, g[1][fi].x);
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(y, kc_im, N1) + within) = pack_h2(g[0][fi].y, g[1][fi].y);
+                if (P == 2) {
+                    const int R1 = nyp + y;
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1) + within) =
+                        pack_h2(g[0][fi].z, g[1][fi].z);
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1) + within) =
+                        pack_h2(g[0][fi].w, g[1][fi].w);
+                }
+            }
+        }
+        __syncthreads();  // sv and the cell lists are reused by the next pass
+        w = wn;
+        buf ^= 1;
+    }
+    if (!ok && tid == 0) {
+        // leave no bulk copy in flight into this block's shared memory
+        for (int b2 = 0; b2 < 2; ++b2)
+            if ((pending >> b2) & 1u) tc::mbar_wait(&bar_raw[b2], (ph >> b2) & 1u, kWaitBudget);
+        atomicExch(a.status, 1);
+    }
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -1105,6 +1304,56 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dftgemm_ws(MmaArgs a)
 
 }  // namespace
 
+// Time samples per chunk so that the grid tiles of one (channel group, time
+// chunk) take at most `budget` bytes, and the tile buffer for them.
+epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
+{
+    const size_t per_t = (size_t)p->tc.cg * p->tc.stride;
+    const int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    const size_t bytes = per_t * tcn;
+    p->chunk_budget = budget;
+    p->tc.tc = tcn;
+    p->time_chunk = tcn;
+    if (p->scratch && bytes == p->scratch_bytes) return EPIC_OK;
+    cudaFree(p->scratch);
+    p->scratch = nullptr;
+    p->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&p->scratch, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(tensor path tile buffer)");
+    p->scratch_bytes = bytes;
+    return EPIC_OK;
+}
+
+// Frames per pass of the persistent gridding kernel and its grid size (the blocks
+// that fit on the GPU at once).  UNSUPPORTED when F frames do not fit in shared memory.
+epic_status dftgemm_grid_config(epic_plan_s* p, int F)
+{
+    if (F != 1 && F != 2 && F != 4 && F != 8) return EPIC_ERR_UNSUPPORTED;
+    const size_t bytes = grid_ps_smem(F, p->A, p->P, p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
+    const void* fn = nullptr;
+    if (p->tc.grid_cplx) {
+        fn = F == 8 ? (const void*)k_dftgemm_grid_ps<true, 8> : F == 4 ? (const void*)k_dftgemm_grid_ps<true, 4>
+           : F == 2 ? (const void*)k_dftgemm_grid_ps<true, 2> : (const void*)k_dftgemm_grid_ps<true, 1>;
+    } else {
+        fn = F == 8 ? (const void*)k_dftgemm_grid_ps<false, 8> : F == 4 ? (const void*)k_dftgemm_grid_ps<false, 4>
+           : F == 2 ? (const void*)k_dftgemm_grid_ps<false, 2> : (const void*)k_dftgemm_grid_ps<false, 1>;
+    }
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_ps)");
+    if (bytes + fa.sharedSizeBytes > (size_t)p->smem_optin) return EPIC_ERR_UNSUPPORTED;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_ps)");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_dftgemm_grid_ps)");
+    if (occ < 1) return EPIC_ERR_UNSUPPORTED;
+    p->tc.grid_frames = F;
+    p->tc.grid_smem = (int)bytes;
+    p->tc.grid_blocks = p->sm_count * occ;
+    return EPIC_OK;
+}
+
 epic_status dftgemm_setup(epic_plan_s* p)
 {
     const int N = p->N, C = p->C, P = p->P;
@@ -1337,37 +1586,45 @@ epic_status dftgemm_setup(epic_plan_s* p)
     for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
     const int per_ch = n_kb * (p->tc.ws ? n_gp : n_s);
-    int cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
-    int tcn = (int)std::max<size_t>(1, kScratchBudget / ((size_t)cg * stride));
-    tcn = std::min(tcn, p->max_time);
-    p->tc.cg = cg;
-    p->tc.tc = tcn;
+    p->tc.cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
     p->tc.stride = stride;
-    p->time_chunk = tcn;
-    p->scratch_bytes = (size_t)cg * tcn * stride;
-    e = cudaMalloc(&p->scratch, p->scratch_bytes);
-    if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(tensor path tile buffer)");
+    epic_status cst = dftgemm_set_chunk(p, kScratchBudget);
+    if (cst != EPIC_OK) return cst;
 
-    // gridding kernel: F frames per pass (4, 2 or 1 as the voltages fit), cell lists in
-    // shared memory when the GCF is real and they fit
+    // gridding kernel: the persistent one when the cell lists of the largest channel fit in
+    // shared memory next to F frames of voltages, else the gather kernel reading them through L1
     int max_cells = 0;
     for (int c = 0; c < C; ++c) max_cells = std::max(max_cells, p->box[c].nx * p->box[c].ny);
-    const size_t max_list = (size_t)p->A * p->K * p->K;
-    const size_t csr_bytes = sizeof(int) * (size_t)((max_cells + 2) & ~1) + sizeof(int2) * max_list;
+    const int max_list = p->A * p->K * p->K;
+    const bool cplx = p->gcf.kind != EPIC_GCF_GAUSSIAN;
+    p->tc.grid_max_cells = max_cells;
+    p->tc.grid_max_list = max_list;
+    p->tc.grid_cplx = cplx;
+    e = cudaSuccess;
+    p->tc.grid_ps = false;
+    for (int gf = 4; gf >= 1 && !p->tc.grid_ps; gf >>= 1) {
+        const epic_status gst = dftgemm_grid_config(p, gf);
+        if (gst == EPIC_OK) p->tc.grid_ps = true;
+        else if (gst != EPIC_ERR_UNSUPPORTED) return gst;
+    }
+    const size_t max_list_l = (size_t)max_list;
+    const size_t csr_bytes = sizeof(int) * (size_t)((max_cells + 2) & ~1) + sizeof(int2) * max_list_l;
     const size_t gl = (size_t)p->smem_optin;
     int gf = 4;
     while (gf > 1 && sizeof(float4) * (size_t)gf * p->A > gl / 2) gf >>= 1;
     size_t sv_bytes = sizeof(float4) * (size_t)gf * p->A;
-    p->tc.grid_csr_smem = p->gcf.kind == EPIC_GCF_GAUSSIAN && sv_bytes + csr_bytes <= gl;
+    p->tc.grid_csr_smem = !cplx && sv_bytes + csr_bytes <= gl;
     if (!p->tc.grid_csr_smem) {
         while (gf > 1 && sizeof(float4) * (size_t)gf * p->A > gl) gf >>= 1;
         sv_bytes = sizeof(float4) * (size_t)gf * p->A;
     }
-    p->tc.grid_frames = gf;
-    p->tc.grid_smem = (int)(sv_bytes + (p->tc.grid_csr_smem ? csr_bytes : 0));
-    if (p->tc.grid_smem > p->smem_optin) {
-        p->last_error = "tensor path: frame of A*P voltages does not fit in shared memory";
-        return EPIC_ERR_UNSUPPORTED;
+    if (!p->tc.grid_ps) {
+        p->tc.grid_frames = gf;
+        p->tc.grid_smem = (int)(sv_bytes + (p->tc.grid_csr_smem ? csr_bytes : 0));
+        if (p->tc.grid_smem > p->smem_optin) {
+            p->last_error = "tensor path: frame of A*P voltages does not fit in shared memory";
+            return EPIC_ERR_UNSUPPORTED;
+        }
     }
 #define EPIC_GRID_ATTR(CS, FF)                                                                                      \
     if (e == cudaSuccess)                                                                                           \
@@ -1426,6 +1683,44 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
+            if (p->tc.grid_ps) {
+                GridArgs g{};
+                g.volt = volt;
+                g.t0 = t0;
+                g.c0 = c0;
+                g.n_ch = ng;
+                g.nt = nt;
+                g.C = C;
+                g.A = A;
+                g.P = P;
+                g.box = p->dt.box;
+                g.cell_off = p->dt.cell_off;
+                g.cell_ptr = p->dt.cell_ptr;
+                g.ce = p->dt.contrib_e;
+                g.cw = p->dt.contrib_w;
+                g.tiles = (uint8_t*)p->scratch;
+                g.tile_stride = p->tc.stride;
+                g.status = p->tc.status;
+                g.max_cells = p->tc.grid_max_cells;
+                g.max_list = p->tc.grid_max_list;
+                g.bulk = ((A * P) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
+                const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
+                ev_begin(p, "k_dftgemm_grid", s);
+#define EPIC_GRID_PS_LAUNCH(CX, FF) k_dftgemm_grid_ps<CX, FF><<<gb, kThreads, p->tc.grid_smem, s>>>(g)
+                if (p->tc.grid_cplx) {
+                    if (F == 8) EPIC_GRID_PS_LAUNCH(true, 8);
+                    else if (F == 4) EPIC_GRID_PS_LAUNCH(true, 4);
+                    else if (F == 2) EPIC_GRID_PS_LAUNCH(true, 2);
+                    else EPIC_GRID_PS_LAUNCH(true, 1);
+                } else {
+                    if (F == 8) EPIC_GRID_PS_LAUNCH(false, 8);
+                    else if (F == 4) EPIC_GRID_PS_LAUNCH(false, 4);
+                    else if (F == 2) EPIC_GRID_PS_LAUNCH(false, 2);
+                    else EPIC_GRID_PS_LAUNCH(false, 1);
+                }
+#undef EPIC_GRID_PS_LAUNCH
+                ev_end(p, s);
+            } else {
             ev_begin(p, "k_dftgemm_grid", s);
 #define EPIC_GRID_LAUNCH(CS, FF)                                                                                    \
     k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box,       \
@@ -1442,6 +1737,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             }
 #undef EPIC_GRID_LAUNCH
             ev_end(p, s);
+            }
             a.c0 = c0;
             a.n_ch = ng;
             a.nt = nt;

@@ -171,6 +171,22 @@ int npt_for(int N, int SW) { return std::max(1, SW * N / kFThreads); }
 
 }  // namespace
 
+// Image columns per work item (slab width SW); its pixels per thread pick the
+// kernel variant.  UNSUPPORTED when SW is not a power of two in 8..min(N, 32)
+// or the shared memory does not hold it.
+epic_status fused_set_slab(epic_plan_s* p, int SW)
+{
+    const int N = p->N;
+    if (SW < 8 || SW > std::min(32, N) || (SW & (SW - 1)) != 0) return EPIC_ERR_UNSUPPORTED;
+    const int npt = npt_for(N, SW);
+    if (npt > 16 || SW * N < kFThreads) return EPIC_ERR_UNSUPPORTED;
+    const size_t bytes = sizeof(float2) * fused_smem_elems(N, p->A, p->P, SW, p->box_max_x, p->box_max_y);
+    if ((int)bytes > p->smem_optin) return EPIC_ERR_UNSUPPORTED;
+    p->slab = SW;
+    p->fused_variant = npt;
+    return EPIC_OK;
+}
+
 epic_status fused_setup(epic_plan_s* p)
 {
     const int N = p->N;

@@ -139,13 +139,33 @@ size_t cols_smem(int N) { return sizeof(float2) * ((size_t)N / 2 + 2ull * col_ti
 
 }  // namespace
 
-epic_status plain_setup(epic_plan_s* p)
+// Time samples per chunk so that the chunk's grids take at most `budget` bytes
+// (at least one sample), and the grid buffer for them.
+epic_status plain_set_chunk(epic_plan_s* p, size_t budget)
 {
     const size_t per_t = (size_t)p->C * p->P * p->N * p->N * sizeof(float2);
-    p->time_chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, kGridBudget / per_t));
-    p->scratch_bytes = per_t * p->time_chunk;
-    cudaError_t e = cudaMalloc(&p->scratch, p->scratch_bytes);
+    const int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    const size_t bytes = per_t * tcn;
+    p->chunk_budget = budget;
+    if (p->scratch && bytes == p->scratch_bytes) {
+        p->time_chunk = tcn;
+        return EPIC_OK;
+    }
+    cudaFree(p->scratch);
+    p->scratch = nullptr;
+    p->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&p->scratch, bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(plain grid buffer)");
+    p->scratch_bytes = bytes;
+    p->time_chunk = tcn;
+    return EPIC_OK;
+}
+
+epic_status plain_setup(epic_plan_s* p)
+{
+    epic_status st = plain_set_chunk(p, kGridBudget);
+    if (st != EPIC_OK) return st;
+    cudaError_t e = cudaSuccess;
     const size_t sg = sizeof(float2) * (size_t)p->A * p->P;
     if (sg > 48 * 1024) {
         if ((int)sg > p->smem_optin) {

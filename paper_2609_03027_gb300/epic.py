@@ -29,6 +29,7 @@ GCF_TABLE = 1
 RESET = 0
 ACCUMULATE = 1
 TIME_KERNELS = 2
+GRAPH = 4
 
 STATUS = {0: "EPIC_OK", 1: "EPIC_ERR_INVALID_ARG", 2: "EPIC_ERR_GRID_OVERFLOW", 3: "EPIC_ERR_OOM",
           4: "EPIC_ERR_BUSY", 5: "EPIC_ERR_TIMEOUT", 6: "EPIC_ERR_CUDA", 7: "EPIC_ERR_UNSUPPORTED",
@@ -38,7 +39,8 @@ STATUS = {0: "EPIC_OK", 1: "EPIC_ERR_INVALID_ARG", 2: "EPIC_ERR_GRID_OVERFLOW", 
 EXPORTED = ["epic_plan_create", "epic_plan_destroy", "epic_image", "epic_image_host", "epic_sync",
             "epic_kernel_times", "epic_plan_get_info", "epic_status_str", "epic_last_error",
             "epic_device_query", "epic_server_create", "epic_server_submit", "epic_server_poll",
-            "epic_server_wait", "epic_server_stats", "epic_server_destroy"]
+            "epic_server_wait", "epic_server_stats", "epic_server_destroy", "epic_plan_tune",
+            "epic_plan_set_param", "epic_plan_get_param", "epic_image_static_scratch"]
 
 
 class EpicError(RuntimeError):
@@ -58,6 +60,11 @@ class _PlanDesc(ctypes.Structure):
                 ("n_chan", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("cell_m", ctypes.POINTER(ctypes.c_double)), ("grid_n", ctypes.c_int), ("gcf", _Gcf),
                 ("path", ctypes.c_int), ("max_time", ctypes.c_int)]
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("n_timed", ctypes.c_int), ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
+                ("n_params", ctypes.c_int), ("names", ctypes.c_char_p * 8), ("values", ctypes.c_int * 8)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -107,6 +114,10 @@ def load(build_if_missing: bool = True):
         L.epic_server_wait.argtypes = [vp, ctypes.c_uint64, i, P(ctypes.c_double)]
         L.epic_server_stats.argtypes = [vp, P(i), P(ctypes.c_double), P(ctypes.c_double), P(i)]
         L.epic_server_destroy.argtypes = [vp]
+        L.epic_plan_tune.argtypes = [vp, vp, i, vp, vp, i, P(_TuneReport)]
+        L.epic_plan_set_param.argtypes = [vp, ctypes.c_char_p, i]
+        L.epic_plan_get_param.argtypes = [vp, ctypes.c_char_p, P(i)]
+        L.epic_image_static_scratch.argtypes = [vp, vp, i, vp, vp, u]
         for name in EXPORTED:
             if name not in ("epic_status_str", "epic_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -185,8 +196,11 @@ class Plan:
             raise EpicError(1, "plan is closed")
         return self._h
 
-    def image(self, volt, out=None, accumulate: bool = False, stream=None, time_kernels: bool = False):
-        """Images of a device voltage block uint8[T][C][A][P] -> float32[C][n_prod][N][N] (device)."""
+    def image(self, volt, out=None, accumulate: bool = False, stream=None, time_kernels: bool = False,
+              graph: bool = False):
+        """Images of a device voltage block uint8[T][C][A][P] -> float32[C][n_prod][N][N] (device).
+
+        ``graph=True`` replays the call's kernels as one recorded CUDA graph (EPIC_GRAPH)."""
         import torch
         if not (isinstance(volt, torch.Tensor) and volt.is_cuda and volt.dtype == torch.uint8):
             raise TypeError("volt must be a CUDA uint8 tensor [T][C][A][P]")
@@ -197,7 +211,7 @@ class Plan:
             out = torch.empty(shape, dtype=torch.float32, device=volt.device)
         elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
             raise ValueError(f"out must be a contiguous CUDA float32 tensor {shape}")
-        flags = (ACCUMULATE if accumulate else RESET) | (TIME_KERNELS if time_kernels else 0)
+        flags = (ACCUMULATE if accumulate else RESET) | (TIME_KERNELS if time_kernels else 0) | (GRAPH if graph else 0)
         T = int(volt.shape[0])
         st = self._lib.epic_image(self._handle(), volt.data_ptr() if T else None, T, _stream_handle(stream),
                                   out.data_ptr(), flags)
@@ -223,11 +237,36 @@ class Plan:
         _check(self._lib, st, self._h)
         return out
 
-    def image_host_ptr(self, volt_ptr: int, T: int, out_ptr: int, accumulate: bool = False, stream=None):
+    def image_host_ptr(self, volt_ptr: int, T: int, out_ptr: int, accumulate: bool = False, stream=None,
+                       graph: bool = False):
         """Host-buffer call on raw host pointers (e.g. pinned torch tensors)."""
-        flags = ACCUMULATE if accumulate else RESET
+        flags = (ACCUMULATE if accumulate else RESET) | (GRAPH if graph else 0)
         st = self._lib.epic_image_host(self._handle(), volt_ptr, int(T), _stream_handle(stream), out_ptr, flags)
         _check(self._lib, st, self._h)
+
+    def tune(self, volt, out=None, reps: int = 3, stream=None) -> Dict[str, object]:
+        """Autotune the plan's tiling on a device block (epic_plan_tune); out is overwritten."""
+        import torch
+        if not (isinstance(volt, torch.Tensor) and volt.is_cuda and volt.dtype == torch.uint8 and volt.is_contiguous()):
+            raise TypeError("volt must be a contiguous CUDA uint8 tensor [T][C][A][P]")
+        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=volt.device)
+        rep = _TuneReport()
+        st = self._lib.epic_plan_tune(self._handle(), volt.data_ptr(), int(volt.shape[0]), _stream_handle(stream),
+                                      out.data_ptr(), int(reps), ctypes.byref(rep))
+        _check(self._lib, st, self._h)
+        params = {rep.names[i].decode(): int(rep.values[i]) for i in range(rep.n_params)}
+        return {"n_timed": rep.n_timed, "default_ms": rep.default_ms, "best_ms": rep.best_ms, "params": params}
+
+    def set_param(self, name: str, value: int):
+        """Set one tuning parameter (epic_plan_set_param)."""
+        _check(self._lib, self._lib.epic_plan_set_param(self._handle(), name.encode(), int(value)), self._h)
+
+    def get_param(self, name: str) -> int:
+        v = ctypes.c_int()
+        _check(self._lib, self._lib.epic_plan_get_param(self._handle(), name.encode(), ctypes.byref(v)), self._h)
+        return int(v.value)
 
     def sync(self):
         _check(self._lib, self._lib.epic_sync(self._handle()), self._h)
