@@ -83,7 +83,7 @@ def kernel_model(name, cfg, T, info):
         return "hbm", grid_bytes + 2 * C * nprod * N * N * 4, "B"
     if name.startswith("k_fused"):
         return "alu", fft_flops_per_block(cfg, T), "flop"
-    if name in ("k_dftgemm_mma", "k_dftgemm_mma_fast", "k_dftgemm_ws"):
+    if name in ("k_dftgemm_mma", "k_dftgemm_mma_fast", "k_dftgemm_ws", "k_dftgemm_ws2", "k_dftgemm_ws3"):
         return "tensor", float(info.get("gemm_flops_per_sample", 0.0)) * T, "flop"
     if name == "k_dftgemm_grid":
         tile = 4 * P * info.get("box_max_x", 0) * info.get("box_max_y", 0)

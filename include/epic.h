@@ -174,7 +174,9 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  * the plan configured with them.  Parameters by path:
  *   PLAIN_FP32    chunk_mb     grid-buffer budget of one time chunk (MiB)
  *   FUSED_FP32    slab         image columns per work item
- *   DFTGEMM_FP16  grid_frames  frames per pass of the gridding kernel;
+ *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
+ *                              control warp does (when the occupied box allows either);
+ *                 grid_frames  frames per pass of the gridding kernel;
  *                 chunk_mb     tile-buffer budget of one (channel group, time chunk)
  * Images after tuning equal those before up to FP32 rounding order.  reps calls
  * are timed per candidate (1..100) after one untimed call.  May reallocate the

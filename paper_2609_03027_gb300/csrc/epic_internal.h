@@ -59,6 +59,7 @@ struct TcState {
     unsigned b2_bytes = 0;
     int d1_cols = 0;
     bool ws = false;               // warp-specialised 64-column-pair kernel
+    int ws_variant = 0;            // 1: epilogue warps issue the MMAs; 2: a control warp does
     uint16_t* a1p = nullptr;       // stage-1 operands per (channel, 64-column kx pair)
     long long* a1p_off = nullptr;
     int n_gp = 0;                  // 64-column pairs per channel
@@ -153,5 +154,6 @@ epic_status dftgemm_setup(epic_plan_s* p);
 epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
 epic_status dftgemm_grid_config(epic_plan_s* p, int F);
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
+epic_status dftgemm_set_kernel(epic_plan_s* p, int variant);
 
 }  // namespace epic

@@ -1302,10 +1302,513 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dftgemm_ws(MmaArgs a)
     if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
 }
 
+// ---------------------------------------------------------------------------------
+// Second warp-specialised kernel: the work item and operands of k_dftgemm_ws, but
+// no thread waits to issue tensor-core work.  The warp that completes a step issues
+// the next one: after every warp has finished epilogue 1 (t) and epilogue 2 (t-1)
+// -- counted on a shared-memory counter -- the last one to arrive issues stage 2
+// of frame t as one MMA chain with N = 128 P (both kx halves, both pols) and
+// stage 1 of frame t+2, so the MMA issue never delays a warp the others wait for.
+// Per frame t, every warp:
+//   wait d1_full(t) -> (warp 0: copy tile t+2 into the buffer S1(t) has read)
+//   -> epilogue 1 (t): D1[t&1] -> FP16 B2[t&1], up to three TMEM loads per wait
+//   -> wait d2_full(t-1) -> epilogue 2 (t-1), four kx per TMEM load
+//   -> arrive; the 16th arrival issues S2(t) -> d2_full and S1(t+2) -> d1_full[t&1]
+// TMEM: D1[0..1] at 0 and d1_cols, A2 at 2 d1_cols, D2 at 256 (N = 128 P columns).
+// Barrier parities follow from the frame index; every thread flips them alike.
+constexpr int kWs2Threads = 512;
+
+// Epilogue 1: D1 columns (chunks [yc0, yc1) of 8 y) of this warp's lane quarter ->
+// B2 rows of half / pol `row0`, up to G TMEM loads per wait.
+template <int G>
+__device__ __forceinline__ void ws2_epilogue1(uint32_t taddr, int nyp, int yc0, int yc1, bool imw, int lane,
+                                              uint8_t* b2, int row0, int R2)
+{
+    const int n0 = row0 + lane, n1 = row0 + 32 + lane;
+    for (int yb = yc0; yb < yc1; yb += G) {
+        const int ng = min(G, yc1 - yb);
+        uint32_t r[8 * G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (g < ng) tmem_ld8(taddr + 8 * (yb + g), r + 8 * g);
+        tc::tmem_wait_ld(r);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g >= ng) break;
+            uint4 pos, neg;
+            pos.x = pack_h2(__uint_as_float(r[8 * g + 0]), __uint_as_float(r[8 * g + 1]));
+            pos.y = pack_h2(__uint_as_float(r[8 * g + 2]), __uint_as_float(r[8 * g + 3]));
+            pos.z = pack_h2(__uint_as_float(r[8 * g + 4]), __uint_as_float(r[8 * g + 5]));
+            pos.w = pack_h2(__uint_as_float(r[8 * g + 6]), __uint_as_float(r[8 * g + 7]));
+            neg.x = pos.x ^ 0x80008000u;
+            neg.y = pos.y ^ 0x80008000u;
+            neg.z = pos.z ^ 0x80008000u;
+            neg.w = pos.w ^ 0x80008000u;
+            const int kc_lo = yb + g, kc_hi = (nyp >> 3) + kc_lo;
+            if (!imw) {
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_lo, R2)) = pos;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_hi, R2)) = pos;
+            } else {
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n0, kc_hi, R2)) = neg;
+                *reinterpret_cast<uint4*>(b2 + sw_chunk(n1, kc_lo, R2)) = pos;
+            }
+        }
+    }
+}
+
+template <int dummy>
+__global__ void __launch_bounds__(kWs2Threads, 1) k_dftgemm_ws2(MmaArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar_a, d1_full[2], d2_full, tile_full[2];
+    __shared__ uint32_t tmem_sh;
+    __shared__ unsigned arrivals;
+    __shared__ int err_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_sh, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_a, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&d1_full[i], 1);
+            tc::mbar_init(&tile_full[i], 1);
+        }
+        tc::mbar_init(&d2_full, 1);
+        arrivals = 0;
+        err_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_sh;
+    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+    uint8_t* sA1 = sbase + a.sA1;
+    uint32_t ph_d1 = 0, ph_tile = 0, ph_a = 0, ph_d2 = 0;
+    bool ok = true;
+    const int P = a.P;
+    const int q4 = warp & 3, j4 = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+    const int R2 = 2 * 64 * P;
+    const uint32_t a2col = 2u * a.d1_cols;
+    const int items = a.n_ch * a.n_kb * a.n_g;
+    const int h2 = j4 >> 1;  // epilogue 2: kx half of this warp, 16 kx at 16 (j4 & 1)
+
+    for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
+        const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
+        const int c = a.c0 + cl;
+        const int4 bx = a.box[c];
+        const int nxp = bx.z, nyp = bx.w;
+        const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
+        const int nt = a.nt;
+        const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
+        const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
+        const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+        const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 128 * P);
+
+        // ---- item prologue: A1 and the first two tiles by the TMA engine, A2 -> TMEM
+        if (tid == 0) {
+            const uint32_t a1_bytes = 256u * pad64(K1);
+            tc::mbar_expect_tx(&bar_a, a1_bytes);
+            tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
+            for (int j = 0; j < 2 && j < nt; ++j) {
+                tc::mbar_expect_tx(&tile_full[j], tile_bytes);
+                tc::bulk_g2s(sbase + a.sB1 + (size_t)j * a.b1_bytes, tiles_c + (size_t)j * frame_step, tile_bytes,
+                             &tile_full[j]);
+            }
+        }
+        if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
+            const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
+            for (int jj = 0; jj < K2 / 2; jj += 8) {
+                uint32_t r[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
+                tc::tmem_st8(tmem + lane_base + a2col + jj, r);
+            }
+            tc::tmem_wait_st();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        auto issue_s1 = [&](int t) {
+            issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
+                     tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
+            tc::mma_commit(&d1_full[t & 1]);
+        };
+        if (tid == 0) {
+            bool good = tc::mbar_wait(&bar_a, ph_a & 1u, kWaitBudget);
+            for (int j = 0; j < 2 && j < nt && good; ++j) {
+                good = tc::mbar_wait(&tile_full[j], (ph_tile >> j) & 1u, kWaitBudget);
+                if (good) {
+                    tc::fence_after_sync();
+                    issue_s1(j);
+                }
+            }
+            if (!good) err_sh = 1;
+        }
+        ph_a ^= 1u;
+        for (int j = 0; j < 2 && j < nt; ++j) ph_tile ^= 1u << j;
+        __syncwarp();
+
+        float axx[16], ayy[16], arx[16], aix[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+        // epilogue-1 part of this warp: lane quarter q4 = (part q4 >> 1, half q4 & 1);
+        // columns: pol j4 >> 1 and half of the y chunks (P = 2), or a quarter of them (P = 1)
+        const int hh = q4 & 1;
+        const bool imw = (q4 >> 1) != 0;
+        const int nyc = nyp >> 3;
+        int p1, yc0, yc1;
+        if (P == 2) {
+            p1 = j4 >> 1;
+            const int mid = (nyc + 1) >> 1;
+            yc0 = (j4 & 1) ? mid : 0;
+            yc1 = (j4 & 1) ? nyc : mid;
+        } else {
+            p1 = 0;
+            yc0 = (nyc * j4) >> 2;
+            yc1 = (nyc * (j4 + 1)) >> 2;
+        }
+        const uint32_t e2addr = tmem + lane_base + 256 + 64 * P * h2 + 16 * (j4 & 1);
+        for (int t = 0; t < nt; ++t) {
+            const int sl = t & 1;
+            // epilogue 1 (t)
+            const bool w = tc::mbar_wait(&d1_full[sl], (ph_d1 >> sl) & 1u, kWaitBudget);
+            ph_d1 ^= 1u << sl;
+            if (!w) err_sh = 1;
+            __syncwarp();
+            tc::fence_after_sync();
+            if (tid == 0 && w && t + 2 < nt) {  // S1(t) has read tile buffer sl: copy tile t+2 into it
+                tc::mbar_expect_tx(&tile_full[sl], tile_bytes);
+                tc::bulk_g2s(sbase + a.sB1 + (size_t)sl * a.b1_bytes, tiles_c + (size_t)(t + 2) * frame_step,
+                             tile_bytes, &tile_full[sl]);
+            }
+            if (w)
+                ws2_epilogue1<3>(tmem + lane_base + sl * a.d1_cols + p1 * nyp, nyp, yc0, yc1, imw, lane,
+                              sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * P * hh + 64 * p1, R2);
+            tc::fence_proxy_async();
+            // epilogue 2 (t-1)
+            if (t >= 1) {
+                const bool w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
+                ph_d2 ^= 1u;
+                if (!w2) err_sh = 1;
+                __syncwarp();
+                tc::fence_after_sync();
+                if (w2) ws_epilogue2(e2addr, P, axx, ayy, arx, aix);
+            }
+            // arrival: the 16th warp issues S2(t) and S1(t+2)
+            tc::fence_before_sync();
+            __syncwarp();
+            unsigned last = 0;
+            if (lane == 0) {
+                __threadfence_block();
+                last = (atomicAdd(&arrivals, 1u) & 15u) == 15u;
+                if (last) __threadfence_block();
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last && lane == 0 && !err_sh) {
+                tc::fence_after_sync();
+                issue_ts(K2 / 16, tmem + 256, tmem + a2col, tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes),
+                         R2 * 128, id2);
+                tc::mma_commit(&d2_full);
+                if (t + 2 < nt) {
+                    if (tc::mbar_wait(&tile_full[sl], (ph_tile >> sl) & 1u, kWaitBudget)) {
+                        tc::fence_after_sync();
+                        issue_s1(t + 2);
+                    } else {
+                        err_sh = 1;
+                    }
+                }
+            }
+            if (t + 2 < nt) ph_tile ^= 1u << sl;
+            __syncwarp();
+            if (__any_sync(0xffffffffu, err_sh != 0)) break;
+        }
+        // epilogue 2 (nt-1)
+        if (nt > 0 && !err_sh) {
+            const bool w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
+            ph_d2 ^= 1u;
+            if (!w2) err_sh = 1;
+            __syncwarp();
+            tc::fence_after_sync();
+            if (w2) ws_epilogue2(e2addr, P, axx, ayy, arx, aix);
+        }
+        tc::fence_before_sync();
+        ok = __syncthreads_and(err_sh == 0) != 0;
+        tc::fence_after_sync();
+        if (!ok) break;
+        // images: row ky = 128 kb + 32 q4 + lane, 16 kx from 64 g + 32 h2 + 16 (j4 & 1)
+        const int ky = 128 * kb + 32 * q4 + lane;
+        const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
+        if (ky < a.N && kx0 < a.N) {
+            const size_t NN = (size_t)a.N * a.N;
+            float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
+            const int nk = min(16, a.N - kx0);
+            store_pixels16(o, nk, a.accumulate, axx);
+            if (a.nprod == 4) {
+                store_pixels16(o + NN, nk, a.accumulate, ayy);
+                store_pixels16(o + 2 * NN, nk, a.accumulate, arx);
+                store_pixels16(o + 3 * NN, nk, a.accumulate, aix);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if ((!ok || err_sh) && tid == 0) atomicExch(a.status, 1);
+}
+
+// ---------------------------------------------------------------------------------
+// Third warp-specialised kernel: 16 epilogue warps and a control warpgroup in
+// separate register budgets (setmaxnreg), so one thread can issue every MMA and
+// tile copy of a frame -- blocking while the tensor pipe is busy -- without holding
+// up any epilogue warp.  Work item, operands and TMEM layout as k_dftgemm_ws2:
+//   control (warp 16, lane 0), per frame t:
+//     wait d1_full(t) -> copy tile t+2 into the buffer S1(t) read;
+//     wait b2_full(t) [and d2_empty(t-1)] -> S2(t) -> d2_full;
+//     wait tile t+2 -> S1(t+2) -> d1_full[t&1]
+//   epilogue warps 0-15, per frame t:
+//     wait d1_full(t) -> epilogue 1 (t) -> arrive b2_full[t&1];
+//     wait d2_full(t-1) -> epilogue 2 (t-1) -> arrive d2_empty
+// Items are separated by two block-wide named barriers (operands loaded; item done).
+constexpr int kWs3Threads = 640;
+
+__device__ __forceinline__ void bar_all(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWs3Threads) : "memory");
+}
+
+template <int dummy>
+__global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar_a, d1_full[2], b2_full[2], d2_full, d2_empty, tile_full[2];
+    __shared__ uint32_t tmem_sh;
+    __shared__ int err_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_sh, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_a, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&d1_full[i], 1);
+            tc::mbar_init(&b2_full[i], 16);
+            tc::mbar_init(&tile_full[i], 1);
+        }
+        tc::mbar_init(&d2_full, 1);
+        tc::mbar_init(&d2_empty, 16);
+        err_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_sh;
+    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+    uint8_t* sA1 = sbase + a.sA1;
+    const int P = a.P;
+    const int R2 = 2 * 64 * P;
+    const uint32_t a2col = 2u * a.d1_cols;
+    const int items = a.n_ch * a.n_kb * a.n_g;
+
+    if (warp >= 16) {
+        // ------------------------------------------------------------ control warpgroup
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
+        uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
+        const bool boss = warp == 16 && lane == 0;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+            const int g = item % a.n_g, cl = item / (a.n_g * a.n_kb);
+            const int c = a.c0 + cl;
+            const int4 bx = a.box[c];
+            const int nxp = bx.z, nyp = bx.w;
+            const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
+            const int nt = a.nt;
+            const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
+            const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
+            const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+            if (boss) {
+                const uint32_t a1_bytes = 256u * pad64(K1);
+                tc::mbar_expect_tx(&bar_a, a1_bytes);
+                tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
+                for (int j = 0; j < 2 && j < nt; ++j) {
+                    tc::mbar_expect_tx(&tile_full[j], tile_bytes);
+                    tc::bulk_g2s(sbase + a.sB1 + (size_t)j * a.b1_bytes, tiles_c + (size_t)j * frame_step, tile_bytes,
+                                 &tile_full[j]);
+                }
+            }
+            bar_all(1);  // A2 is in TMEM
+            if (boss) {
+                const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 128 * P);
+                auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
+                    const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
+                    ph ^= 1u << slot;
+                    return r;
+                };
+                auto issue_s1 = [&](int t) {
+                    issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
+                             tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
+                    tc::mma_commit(&d1_full[t & 1]);
+                };
+                bool good = wait_bit(&bar_a, ph_a, 0);
+                for (int j = 0; j < 2 && j < nt && good; ++j) {
+                    good = wait_bit(&tile_full[j], ph_tile, j);
+                    if (good) {
+                        tc::fence_after_sync();
+                        issue_s1(j);
+                    }
+                }
+                for (int t = 0; t < nt && good; ++t) {
+                    const int sl = t & 1;
+                    good = wait_bit(&d1_full[sl], ph_d1, sl);  // S1(t) done: its tile buffer is free
+                    if (!good) break;
+                    if (t + 2 < nt) {
+                        tc::mbar_expect_tx(&tile_full[sl], tile_bytes);
+                        tc::bulk_g2s(sbase + a.sB1 + (size_t)sl * a.b1_bytes, tiles_c + (size_t)(t + 2) * frame_step,
+                                     tile_bytes, &tile_full[sl]);
+                    }
+                    good = wait_bit(&b2_full[sl], ph_b2, sl);
+                    if (good && t >= 1) good = wait_bit(&d2_empty, ph_e2, 0);
+                    if (!good) break;
+                    tc::fence_after_sync();
+                    issue_ts(K2 / 16, tmem + 256, tmem + a2col, tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes),
+                             R2 * 128, id2);
+                    tc::mma_commit(&d2_full);
+                    if (t + 2 < nt) {
+                        good = wait_bit(&tile_full[sl], ph_tile, sl);
+                        if (!good) break;
+                        tc::fence_after_sync();
+                        issue_s1(t + 2);
+                    }
+                }
+                if (!good) err_sh = 1;
+            }
+            __syncwarp();
+            bar_all(2);  // item done
+            if (err_sh) break;
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue warps
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 112;" ::: "memory");
+        uint32_t ph_d1 = 0, ph_d2 = 0;
+        const int q4 = warp & 3, j4 = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+        const int h2 = j4 >> 1;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+            const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
+            const int c = a.c0 + cl;
+            const int4 bx = a.box[c];
+            const int nyp = bx.w;
+            const int K2 = 2 * nyp;
+            const int nt = a.nt;
+            if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
+                const uint32_t* src =
+                    a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
+                for (int jj = 0; jj < K2 / 2; jj += 8) {
+                    uint32_t r[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
+                    tc::tmem_st8(tmem + lane_base + a2col + jj, r);
+                }
+                tc::tmem_wait_st();
+            }
+            tc::fence_before_sync();
+            bar_all(1);
+            tc::fence_after_sync();
+            float axx[16], ayy[16], arx[16], aix[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+            const int hh = q4 & 1;
+            const bool imw = (q4 >> 1) != 0;
+            const int nyc = nyp >> 3;
+            int p1, yc0, yc1;
+            if (P == 2) {
+                p1 = j4 >> 1;
+                const int mid = (nyc + 1) >> 1;
+                yc0 = (j4 & 1) ? mid : 0;
+                yc1 = (j4 & 1) ? nyc : mid;
+            } else {
+                p1 = 0;
+                yc0 = (nyc * j4) >> 2;
+                yc1 = (nyc * (j4 + 1)) >> 2;
+            }
+            const uint32_t e2addr = tmem + lane_base + 256 + 64 * P * h2 + 16 * (j4 & 1);
+            bool live = true;
+            for (int t = 0; t < nt && live; ++t) {
+                const int sl = t & 1;
+                const bool w = tc::mbar_wait(&d1_full[sl], (ph_d1 >> sl) & 1u, kWaitBudget);
+                ph_d1 ^= 1u << sl;
+                __syncwarp();
+                tc::fence_after_sync();
+                if (w)
+                    ws2_epilogue1<2>(tmem + lane_base + sl * a.d1_cols + p1 * nyp, nyp, yc0, yc1, imw, lane,
+                                  sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * P * hh + 64 * p1, R2);
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&b2_full[sl]);
+                bool w2 = true;
+                if (t >= 1) {
+                    w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
+                    ph_d2 ^= 1u;
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    if (w2) ws_epilogue2(e2addr, P, axx, ayy, arx, aix);
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&d2_empty);
+                }
+                if (!w || !w2) err_sh = 1;
+                live = !__any_sync(0xffffffffu, err_sh != 0);
+            }
+            if (nt > 0 && live) {
+                const bool w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
+                ph_d2 ^= 1u;
+                if (!w2) err_sh = 1;
+                __syncwarp();
+                tc::fence_after_sync();
+                if (w2) ws_epilogue2(e2addr, P, axx, ayy, arx, aix);
+            }
+            tc::fence_before_sync();
+            bar_all(2);
+            tc::fence_after_sync();
+            if (err_sh) break;
+            // images: row ky = 128 kb + 32 q4 + lane, 16 kx from 64 g + 32 h2 + 16 (j4 & 1)
+            const int ky = 128 * kb + 32 * q4 + lane;
+            const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
+            if (ky < a.N && kx0 < a.N) {
+                const size_t NN = (size_t)a.N * a.N;
+                float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
+                const int nk = min(16, a.N - kx0);
+                store_pixels16(o, nk, a.accumulate, axx);
+                if (a.nprod == 4) {
+                    store_pixels16(o + NN, nk, a.accumulate, ayy);
+                    store_pixels16(o + 2 * NN, nk, a.accumulate, arx);
+                    store_pixels16(o + 3 * NN, nk, a.accumulate, aix);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (err_sh && tid == 0) atomicExch(a.status, 1);
+}
+
 }  // namespace
 
 // Time samples per chunk so that the grid tiles of one (channel group, time
 // chunk) take at most `budget` bytes, and the tile buffer for them.
+epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
+{
+    if (!p->tc.ws || variant < 1 || variant > 3) return EPIC_ERR_UNSUPPORTED;
+    p->tc.ws_variant = variant;
+    return EPIC_OK;
+}
+
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
 {
     const size_t per_t = (size_t)p->tc.cg * p->tc.stride;
@@ -1639,6 +2142,9 @@ epic_status dftgemm_setup(epic_plan_s* p)
 #undef EPIC_GRID_ATTR
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
     e = cudaFuncSetAttribute(k_dftgemm_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_ws2<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_ws3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    p->tc.ws_variant = p->tc.ws ? 3 : 0;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma_fast<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
@@ -1744,10 +2250,13 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             a.accumulate = (accumulate || t0 > 0) ? 1 : 0;
             const int items = ng * a.n_kb * (p->tc.ws ? p->tc.n_gp : a.n_s);
             const int grid = std::min(items, p->sm_count);
-            ev_begin(p, p->tc.ws ? "k_dftgemm_ws" : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
+            ev_begin(p, p->tc.ws ? (p->tc.ws_variant == 3 ? "k_dftgemm_ws3" : p->tc.ws_variant == 2 ? "k_dftgemm_ws2" : "k_dftgemm_ws")
+                                 : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
             if (p->tc.ws) {
                 a.n_g = p->tc.n_gp;
-                k_dftgemm_ws<0><<<grid, kWsThreads, p->tc.smem, s>>>(a);
+                if (p->tc.ws_variant == 3) k_dftgemm_ws3<0><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                else if (p->tc.ws_variant == 2) k_dftgemm_ws2<0><<<grid, kWs2Threads, p->tc.smem, s>>>(a);
+                else k_dftgemm_ws<0><<<grid, kWsThreads, p->tc.smem, s>>>(a);
             } else if (p->tc.fast) k_dftgemm_mma_fast<0><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             else if (p->tc.nb == 2) k_dftgemm_mma<2><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
             else k_dftgemm_mma<1><<<grid, kMmaThreads, p->tc.smem, s>>>(a);
