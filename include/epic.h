@@ -176,6 +176,8 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  *   FUSED_FP32    slab         image columns per work item
  *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
  *                              control warp does (when the occupied box allows either);
+ *                 grid_kernel  gridding kernel: 1 row-major cell walk, 2 cells in lists sorted
+ *                              by length (Gaussian GCF, when its tiles fit in shared memory);
  *                 grid_frames  frames per pass of the gridding kernel;
  *                 chunk_mb     tile-buffer budget of one (channel group, time chunk)
  * Images after tuning equal those before up to FP32 rounding order.  reps calls

@@ -56,6 +56,8 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.a2w_off);
     cudaFree(p->tc.a1p);
     cudaFree(p->tc.a1p_off);
+    cudaFree(p->tc.gtask);
+    cudaFree(p->tc.gtask_off);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);
     cudaFree(p->stage_out);

@@ -53,6 +53,10 @@ struct TcState {
     int grid_blocks = 0;           // blocks of the persistent gridding kernel
     int grid_max_cells = 0;        // largest occupied box (cells)
     int grid_max_list = 0;         // (cell, element) entries per channel
+    int grid_variant = 1;          // 1: persistent row-major gather, 2: balanced task lists
+    int2* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
+    int* gtask_off = nullptr;      // [C + 1]
+    int gtask_max = 0;             // largest task list
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2
     uint32_t* a2w = nullptr;       // stage-2 operand rows as packed FP16 pairs (fast variant)
     long long* a2w_off = nullptr;
@@ -155,5 +159,6 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
 epic_status dftgemm_grid_config(epic_plan_s* p, int F);
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant);
+epic_status dftgemm_set_grid_kernel(epic_plan_s* p, int variant);
 
 }  // namespace epic

@@ -463,6 +463,196 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
     }
 }
 
+// Balanced gridding kernel (real GCF weights): the gather of k_dftgemm_grid_ps,
+// but each thread works on single non-empty cells taken from a per-channel task
+// list sorted by contribution count, so the 32 lanes of a warp walk lists of
+// nearly equal length (a row-major walk keeps about 40% of the lanes busy), and
+// the F frames of a pass are assembled in shared-memory tiles that the TMA
+// engine then stores with one bulk copy per frame.  Tile buffers are double
+// buffered across passes; cells no task touches stay zero from the channel's
+// first pass.
+constexpr int kGridBalThreads = 512;
+
+struct GridBalArgs {
+    GridArgs g;
+    const int2* tasks;      // per channel: (cell | count << 24, first entry) sorted by count
+    const int* task_off;    // [C + 1]
+    int max_tasks;          // largest task count of a channel
+    unsigned tile_max;      // shared-memory bytes per tile (largest channel)
+};
+
+__host__ __device__ inline size_t grid_bal_smem(int F, int A, int P, int max_tasks, int max_list, unsigned tile_max)
+{
+    const size_t ap = (size_t)((A * P + 15) & ~15);
+    size_t b = 2ull * F * ap + 16ull * F * A;  // raw voltages, unpacked voltages
+    b = (b + 127) & ~(size_t)127;
+    b += 2ull * F * tile_max;                  // tile buffers
+    b += 8ull * max_tasks + 8ull * max_list;   // task list, (element, weight) entries
+    return b;
+}
+
+__device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
+{
+    return (uint32_t)((k >> 6) * (N1 * 128) + R * 128 + ((((k >> 3) & 7) ^ (R & 7)) << 4) + ((k & 7) << 1));
+}
+
+template <int F>
+__global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBalArgs ba)
+{
+    const GridArgs& a = ba.g;
+    extern __shared__ __align__(128) uint8_t gsm[];
+    __shared__ uint64_t bar_raw[2];
+    const int tid = threadIdx.x;
+    const int A = a.A, P = a.P, AP = A * P;
+    const int APr = (AP + 15) & ~15;
+    uint8_t* raw = gsm;                                                // [2][F][APr]
+    float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);         // [F][A]
+    const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
+    uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
+    int2* stask = reinterpret_cast<int2*>(stile + 2ull * F * ba.tile_max);
+    int2* con = stask + ba.max_tasks;
+
+    const long long W = (long long)a.n_ch * a.nt;
+    const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+    if (tid == 0) {
+        tc::mbar_init(&bar_raw[0], 1);
+        tc::mbar_init(&bar_raw[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (w0 >= w1) return;
+
+    auto pass_len = [&](long long w) {
+        const int f = (int)(w % a.nt);
+        return (int)min((long long)min(F, a.nt - f), w1 - w);
+    };
+    auto fetch = [&](long long w, int b) {  // thread 0: raw bytes of the pass starting at w -> buffer b
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        tc::mbar_expect_tx(&bar_raw[b], (uint32_t)(nf * AP));
+        for (int i = 0; i < nf; ++i)
+            tc::bulk_g2s(raw + (size_t)(b * F + i) * APr,
+                         a.volt + ((size_t)(a.t0 + f + i) * a.C + a.c0 + cl) * (size_t)AP, (uint32_t)AP, &bar_raw[b]);
+    };
+
+    uint32_t ph = 0, pending = 0;
+    int staged = -1, buf = 0, tb = 0, ntask = 0;
+    bool ok = true;
+    if (a.bulk && tid == 0) {
+        fetch(w0, 0);
+        pending = 1u;
+    }
+    for (long long w = w0; w < w1;) {
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        const long long wn = w + nf;
+        const int c = a.c0 + cl;
+        const int4 b = a.box[c];
+        const int nxp = b.z, nyp = b.w, N1 = P * nyp;
+        const uint32_t tile_bytes = (uint32_t)N1 * pad64(2 * nxp) * 2;
+        if (a.bulk && tid == 0 && wn < w1) {
+            fetch(wn, buf ^ 1);
+            pending |= 1u << (buf ^ 1);
+        }
+        if (cl != staged) {  // new channel: zeroed tile buffers, its task list and entries
+            if (tid == 0) tc::bulk_wait_read<0>();
+            __syncthreads();
+            const int nz = (int)((2ull * F * ba.tile_max) >> 4);
+            for (int i = tid; i < nz; i += blockDim.x) reinterpret_cast<uint4*>(stile)[i] = make_uint4(0, 0, 0, 0);
+            const int t0 = ba.task_off[c];
+            ntask = ba.task_off[c + 1] - t0;
+            for (int i = tid; i < ntask; i += blockDim.x) stask[i] = ba.tasks[t0 + i];
+            const int* gptr = a.cell_ptr + a.cell_off[c];
+            const int base = gptr[0];
+            const int ncon = gptr[nxp * nyp] - base;
+            for (int i = tid; i < ncon; i += blockDim.x)
+                con[i] = make_int2(a.ce[base + i], __float_as_int(a.cw[base + i].x));
+            staged = cl;
+        }
+        if (a.bulk) {
+            const bool got = tc::mbar_wait(&bar_raw[buf], (ph >> buf) & 1u, kWaitBudget);
+            if (got) {
+                ph ^= 1u << buf;
+                pending &= ~(1u << buf);
+            }
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+            for (int i = tid; i < nf * A; i += blockDim.x) {
+                const int fi = i / A, e = i - fi * A;
+                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr + (size_t)e * P;
+                const float2 x = unpack44(fr[0]);
+                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+            }
+        } else {
+            for (int i = tid; i < nf * A; i += blockDim.x) {
+                const int fi = i / A, e = i - fi * A;
+                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP + (size_t)e * P;
+                const float2 x = unpack44(fr[0]);
+                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+            }
+        }
+        if (tid == 0) tc::bulk_wait_read<1>();  // the stores of the pass before last have read tile buffer tb
+        __syncthreads();
+        uint8_t* tset = stile + (size_t)tb * F * ba.tile_max;
+        for (int s = tid; s < ntask; s += blockDim.x) {
+            const int2 tk = stask[s];
+            const int r = tk.x & 0xFFFFFF, n = (int)((unsigned)tk.x >> 24);
+            const int y = r / nxp, x = r - y * nxp;
+            float4 g[F];
+#pragma unroll
+            for (int fi = 0; fi < F; ++fi) g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = tk.y; q < tk.y + n; ++q) {
+                const int2 cr = con[q];
+                const float wv = __int_as_float(cr.y);
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) {
+                    if (fi < nf) {
+                        const float4 v = sv[fi * A + cr.x];
+                        g[fi].x = fmaf(wv, v.x, g[fi].x);
+                        g[fi].y = fmaf(wv, v.y, g[fi].y);
+                        g[fi].z = fmaf(wv, v.z, g[fi].z);
+                        g[fi].w = fmaf(wv, v.w, g[fi].w);
+                    }
+                }
+            }
+            const uint32_t o_rx = tile_half_off(y, x, N1), o_ix = tile_half_off(y, nxp + x, N1);
+            const uint32_t o_ry = tile_half_off(nyp + y, x, N1), o_iy = tile_half_off(nyp + y, nxp + x, N1);
+#pragma unroll
+            for (int fi = 0; fi < F; ++fi) {
+                if (fi >= nf) break;
+                uint8_t* t = tset + (size_t)fi * ba.tile_max;
+                *reinterpret_cast<__half*>(t + o_rx) = __float2half_rn(g[fi].x);
+                *reinterpret_cast<__half*>(t + o_ix) = __float2half_rn(g[fi].y);
+                if (P == 2) {
+                    *reinterpret_cast<__half*>(t + o_ry) = __float2half_rn(g[fi].z);
+                    *reinterpret_cast<__half*>(t + o_iy) = __float2half_rn(g[fi].w);
+                }
+            }
+        }
+        tc::fence_proxy_async();  // tile writes -> visible to the bulk copies
+        __syncthreads();
+        if (tid == 0) {
+            for (int fi = 0; fi < nf; ++fi)
+                tc::bulk_s2g(a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride, tset + (size_t)fi * ba.tile_max,
+                             tile_bytes);
+            tc::bulk_commit();
+        }
+        w = wn;
+        buf ^= 1;
+        tb ^= 1;
+    }
+    if (tid == 0) {
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // tile stores complete
+        if (!ok) {
+            for (int b2 = 0; b2 < 2; ++b2)
+                if ((pending >> b2) & 1u) tc::mbar_wait(&bar_raw[b2], (ph >> b2) & 1u, kWaitBudget);
+            atomicExch(a.status, 1);
+        }
+    }
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -1827,10 +2017,13 @@ epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
     return EPIC_OK;
 }
 
+static epic_status grid_bal_config(epic_plan_s* p, int F);
+
 // Frames per pass of the persistent gridding kernel and its grid size (the blocks
 // that fit on the GPU at once).  UNSUPPORTED when F frames do not fit in shared memory.
 epic_status dftgemm_grid_config(epic_plan_s* p, int F)
 {
+    if (p->tc.grid_variant == 2) return grid_bal_config(p, F);
     if (F != 1 && F != 2 && F != 4 && F != 8) return EPIC_ERR_UNSUPPORTED;
     const size_t bytes = grid_ps_smem(F, p->A, p->P, p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
     const void* fn = nullptr;
@@ -1855,6 +2048,49 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F)
     p->tc.grid_smem = (int)bytes;
     p->tc.grid_blocks = p->sm_count * occ;
     return EPIC_OK;
+}
+
+// Frames per pass and grid size of the balanced gridding kernel (UNSUPPORTED when
+// F tile buffers, the task list and the entries do not fit in shared memory).
+static epic_status grid_bal_config(epic_plan_s* p, int F)
+{
+    if (!p->tc.gtask || (F != 1 && F != 2 && F != 4)) return EPIC_ERR_UNSUPPORTED;
+    const size_t bytes =
+        grid_bal_smem(F, p->A, p->P, p->tc.gtask_max, p->tc.grid_max_list, (unsigned)p->tc.stride);
+    const void* fn = F == 4 ? (const void*)k_dftgemm_grid_bal<4>
+                   : F == 2 ? (const void*)k_dftgemm_grid_bal<2> : (const void*)k_dftgemm_grid_bal<1>;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_bal)");
+    if (bytes + fa.sharedSizeBytes > (size_t)p->smem_optin) return EPIC_ERR_UNSUPPORTED;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_bal)");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridBalThreads, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_dftgemm_grid_bal)");
+    if (occ < 1) return EPIC_ERR_UNSUPPORTED;
+    p->tc.grid_frames = F;
+    p->tc.grid_smem = (int)bytes;
+    p->tc.grid_blocks = p->sm_count * occ;
+    return EPIC_OK;
+}
+
+// Gridding kernel variant: 1 = persistent row-major gather, 2 = balanced task lists.
+// Keeps the frames per pass if the variant allows them, else the largest it allows.
+epic_status dftgemm_set_grid_kernel(epic_plan_s* p, int variant)
+{
+    if (variant != 1 && variant != 2) return EPIC_ERR_UNSUPPORTED;
+    if (variant == 2 && !p->tc.gtask) return EPIC_ERR_UNSUPPORTED;
+    if (variant == 1 && !p->tc.grid_ps) return EPIC_ERR_UNSUPPORTED;
+    const int old_variant = p->tc.grid_variant, old_f = p->tc.grid_frames;
+    p->tc.grid_variant = variant;
+    epic_status st = EPIC_ERR_UNSUPPORTED;
+    for (int F = old_f; F >= 1 && st == EPIC_ERR_UNSUPPORTED; F >>= 1) st = dftgemm_grid_config(p, F);
+    if (st != EPIC_OK) {
+        p->tc.grid_variant = old_variant;
+        dftgemm_grid_config(p, old_f);
+    }
+    return st;
 }
 
 epic_status dftgemm_setup(epic_plan_s* p)
@@ -2105,10 +2341,57 @@ epic_status dftgemm_setup(epic_plan_s* p)
     p->tc.grid_cplx = cplx;
     e = cudaSuccess;
     p->tc.grid_ps = false;
+    p->tc.grid_variant = 1;
     for (int gf = 4; gf >= 1 && !p->tc.grid_ps; gf >>= 1) {
         const epic_status gst = dftgemm_grid_config(p, gf);
         if (gst == EPIC_OK) p->tc.grid_ps = true;
         else if (gst != EPIC_ERR_UNSUPPORTED) return gst;
+    }
+    if (!cplx) {  // per-channel task lists of non-empty cells, longest list first
+        std::vector<int> coff, cptr, ce;
+        std::vector<float2> cw;
+        build_csr(p, coff, cptr, ce, cw);
+        std::vector<int2> tasks;
+        std::vector<int> toff(C + 1, 0);
+        bool fits = true;
+        int tmax = 0;
+        for (int c = 0; c < C && fits; ++c) {
+            toff[c] = (int)tasks.size();
+            const int* ptr = &cptr[coff[c]];
+            const int ncell = p->box[c].nx * p->box[c].ny;
+            std::vector<int> idx;
+            for (int r = 0; r < ncell; ++r)
+                if (ptr[r + 1] > ptr[r]) idx.push_back(r);
+            std::stable_sort(idx.begin(), idx.end(),
+                             [&](int u, int v) { return ptr[u + 1] - ptr[u] > ptr[v + 1] - ptr[v]; });
+            for (int r : idx) {
+                const int n = ptr[r + 1] - ptr[r];
+                if (n > 255 || r >= (1 << 24)) fits = false;
+                tasks.push_back(make_int2(r | (n << 24), ptr[r] - ptr[0]));
+            }
+            tmax = std::max(tmax, (int)idx.size());
+        }
+        toff[C] = (int)tasks.size();
+        if (fits && !tasks.empty()) {
+            e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int2));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int2),
+                                                 cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gtask_off, toff.size() * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask_off, toff.data(), toff.size() * sizeof(int),
+                                                 cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(p, e, "gridding task lists upload");
+            p->tc.gtask_max = tmax;
+            p->dt.dft_bytes += tasks.size() * sizeof(int2) + toff.size() * sizeof(int);
+            const int keep_f = p->tc.grid_frames;
+            p->tc.grid_variant = 2;
+            epic_status bst = EPIC_ERR_UNSUPPORTED;
+            for (int gf = 2; gf >= 1 && bst == EPIC_ERR_UNSUPPORTED; gf >>= 1) bst = grid_bal_config(p, gf);
+            if (bst != EPIC_OK) {
+                if (bst != EPIC_ERR_UNSUPPORTED) return bst;
+                p->tc.grid_variant = 1;
+                if (p->tc.grid_ps) dftgemm_grid_config(p, keep_f);
+            }
+        }
     }
     const size_t max_list_l = (size_t)max_list;
     const size_t csr_bytes = sizeof(int) * (size_t)((max_cells + 2) & ~1) + sizeof(int2) * max_list_l;
@@ -2189,7 +2472,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
-            if (p->tc.grid_ps) {
+            if (p->tc.grid_ps || p->tc.grid_variant == 2) {
                 GridArgs g{};
                 g.volt = volt;
                 g.t0 = t0;
@@ -2212,6 +2495,17 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 g.bulk = ((A * P) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
                 const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
                 ev_begin(p, "k_dftgemm_grid", s);
+                if (p->tc.grid_variant == 2) {
+                    GridBalArgs ba{};
+                    ba.g = g;
+                    ba.tasks = p->tc.gtask;
+                    ba.task_off = p->tc.gtask_off;
+                    ba.max_tasks = p->tc.gtask_max;
+                    ba.tile_max = (unsigned)p->tc.stride;
+                    if (F == 4) k_dftgemm_grid_bal<4><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
+                    else if (F == 2) k_dftgemm_grid_bal<2><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
+                    else k_dftgemm_grid_bal<1><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
+                } else {
 #define EPIC_GRID_PS_LAUNCH(CX, FF) k_dftgemm_grid_ps<CX, FF><<<gb, kThreads, p->tc.grid_smem, s>>>(g)
                 if (p->tc.grid_cplx) {
                     if (F == 8) EPIC_GRID_PS_LAUNCH(true, 8);
@@ -2223,6 +2517,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     else if (F == 4) EPIC_GRID_PS_LAUNCH(false, 4);
                     else if (F == 2) EPIC_GRID_PS_LAUNCH(false, 2);
                     else EPIC_GRID_PS_LAUNCH(false, 1);
+                }
                 }
 #undef EPIC_GRID_PS_LAUNCH
                 ev_end(p, s);

@@ -88,6 +88,14 @@ def test_gridding_frames_per_pass_bitwise_identical():
         first = next(iter(outs.values()))
         for F, o in outs.items():
             assert np.array_equal(o, first), F
+        # both gridding kernels (row-major walk, length-sorted cell lists) alike
+        for gk in (1, 2):
+            try:
+                plan.set_param("grid_kernel", gk)
+            except E.EpicError as ex:
+                assert ex.status in (7, 8)
+                continue
+            assert np.array_equal(plan.image(v).cpu().numpy(), first), gk
         # voltage block at an address that is not 16-byte aligned: no bulk copies
         raw = torch.zeros(v.numel() + 16, dtype=torch.uint8, device="cuda")
         va = raw[1:1 + v.numel()].view(v.shape)
