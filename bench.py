@@ -17,6 +17,7 @@ Prints one JSON line (rank 0).  Under torchrun every rank images its own block
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -257,6 +258,86 @@ def run_e2e(E, cfg, volt, out, T, units, world, dev, args, tuning=None):
             "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": 1e3 * e2e_s}
 
 
+# ----------------------------------------------------------------------------- serving (streaming mix)
+
+SERVE_CHANNELS = (32, 64, 128, 256, 384)
+SERVE_DF_HZ = 25e3
+
+
+def serving_plans_spec():
+    """(name, config) of every (station type, channel count) of the streaming mix: the
+    64/256/1024/4096-element station types, C contiguous 25 kHz channels from each
+    type's first frequency."""
+    out = []
+    for st in synth.mixed_station_types():
+        for C in SERVE_CHANNELS:
+            cfg = dataclasses.replace(st, name=f"{st.name}-{C}ch")
+            cfg.freq_hz = st.freq_hz[0] + np.arange(C) * SERVE_DF_HZ
+            out.append(cfg)
+    return out
+
+
+def run_serving(E, args, dev):
+    """Poisson arrivals (mean 10 ms) of blocks from the station mix for args.serve_seconds,
+    imaged by the continuous-batching server; p50/p99 latency and pixel-updates/s."""
+    import torch
+    rng = np.random.default_rng(5)
+    specs = serving_plans_spec()
+    plans, outs, blocks = [], [], []
+    for cfg in specs:
+        plans.append(E.Plan.from_config(cfg, path=args.path, max_time=cfg.n_time))
+        outs.append(torch.empty((cfg.n_chan, cfg.n_prod, cfg.grid_n, cfg.grid_n), dtype=torch.float32, device=dev))
+        n = cfg.voltage_bytes()
+        d = torch.randint(0, 256, (n,), dtype=torch.uint8, device=dev)
+        h = torch.empty(n, dtype=torch.uint8).pin_memory()
+        h.copy_(d)
+        blocks.append(h)
+        del d
+    torch.cuda.synchronize()
+    pool = 2 * max(b.numel() for b in blocks) + (256 << 20)
+    n_types = len(synth.mixed_station_types())
+    arrivals, t = [], 0.0
+    while t < args.serve_seconds:
+        t += rng.exponential(0.010)
+        arrivals.append((t, int(rng.integers(0, n_types)) * len(SERVE_CHANNELS) + int(rng.integers(0, len(SERVE_CHANNELS)))))
+    tickets = []
+    with E.Server(device_bytes=pool, slots=4) as srv:
+        for k in range(len(specs)):              # warm-up: every plan's first block outside the window
+            tk = None
+            while tk is None:
+                tk = srv.submit_ptr(plans[k], blocks[k].data_ptr(), specs[k].n_time, outs[k])
+            srv.wait(tk)
+        srv_base = srv.stats()["completed"]
+        t0 = time.perf_counter()
+        for at, k in arrivals:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            tk = None
+            while tk is None:
+                tk = srv.submit_ptr(plans[k], blocks[k].data_ptr(), specs[k].n_time, outs[k])
+                if tk is None:
+                    time.sleep(2e-4)
+            tickets.append((tk, at, time.perf_counter() - t0, k))
+        lat_arrival, units = [], 0
+        for tk, at, sub, k in tickets:
+            lat = srv.wait(tk, timeout_ms=600000)
+            lat_arrival.append(1e3 * (sub - at) + lat)
+            units += specs[k].pixel_updates()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    for p in plans:
+        p.close()
+    la = np.array(lat_arrival)
+    return {"workload": "streaming mix: 64/256/1024/4096-el dual-pol stations, C in {32,64,128,256,384} x 25 kHz, "
+                        "Poisson arrivals mean 10 ms",
+            "seconds": args.serve_seconds, "blocks": len(tickets), "value": units / wall, "unit": UNIT,
+            "p50_ms": float(np.percentile(la, 50)), "p99_ms": float(np.percentile(la, 99)),
+            "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+            "latency": "from arrival (incl. admission wait) to completion; server_* from submission",
+            "completed": st["completed"] - srv_base}
+
+
 # ----------------------------------------------------------------------------- main
 
 def main():
@@ -274,6 +355,8 @@ def main():
     ap.add_argument("--time", type=int, default=0, help="override the block length T (small profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (plan defaults)")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the streaming-mix serving run (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -377,6 +460,13 @@ def main():
     if args.e2e_steps > 0:
         e2e = run_e2e(E, cfg, volt, out, T, units, world, dev, args, info.get("tuning"))
 
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        try:
+            serving = run_serving(E, args, dev)
+        except Exception as ex:  # reported, never fatal to the throughput line
+            serving = {"error": f"{type(ex).__name__}: {ex}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, volt)
@@ -392,7 +482,7 @@ def main():
                            "launch": "cuda-graph" if use_graph else "per-kernel",
                            "tuning": info.get("tuning")},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
-                "cpu_baseline": cpu, "compare": compare}
+                "cpu_baseline": cpu, "compare": compare, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -335,6 +335,17 @@ class Server:
         self._keep[t.value] = (v, out)
         return int(t.value)
 
+    def submit_ptr(self, plan: "Plan", volt_ptr: int, T: int, out, accumulate: bool = False) -> Optional[int]:
+        """Queue a block given by a raw host pointer (e.g. a pinned tensor the caller keeps
+        alive and unchanged until the ticket completes); None when the server is busy."""
+        t = ctypes.c_uint64()
+        st = self._lib.epic_server_submit(self._h, plan._handle(), volt_ptr, int(T), out.data_ptr(),
+                                          ACCUMULATE if accumulate else RESET, ctypes.byref(t))
+        if st == 4:  # EPIC_ERR_BUSY
+            return None
+        _check(self._lib, st)
+        return int(t.value)
+
     def poll(self, ticket: int) -> Tuple[bool, float]:
         d, lat = ctypes.c_int(), ctypes.c_double()
         _check(self._lib, self._lib.epic_server_poll(self._h, ticket, ctypes.byref(d), ctypes.byref(lat)))

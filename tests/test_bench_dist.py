@@ -1,0 +1,45 @@
+"""Multi-rank plumbing of bench.py on CPU: two gloo ranks (127.0.0.1) run the
+replica path's barrier and max-over-ranks reduction, and rank 0's aggregate
+equals the units of all ranks over the slowest rank's time (weak scaling)."""
+import os
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank), EPIC_BENCH_BACKEND="gloo")
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, _ = bench.dist_setup()
+    assert (w, r) == (world, rank)
+    bench.barrier(w)
+    step_s = 0.010 * (rank + 1)                   # rank 1 is the slower one
+    slowest = bench.reduce_max(step_s, w)
+    units = 1000
+    value = units * w / slowest
+    q.put((rank, slowest, value))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_max_and_weak_scaling_aggregate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 2000)
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, slowest, value in res:
+        assert slowest == pytest.approx(0.020)
+        assert value == pytest.approx(2 * 1000 / 0.020)
