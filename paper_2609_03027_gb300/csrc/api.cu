@@ -84,6 +84,14 @@ epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what)
     return e == cudaErrorMemoryAllocation ? EPIC_ERR_OOM : EPIC_ERR_CUDA;
 }
 
+cudaError_t allow_max_smem(const void* fn, int optin)
+{
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s)
 {
     if (!p->timing) return;

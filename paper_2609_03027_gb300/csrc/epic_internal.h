@@ -137,6 +137,11 @@ void build_csr(const epic_plan_s* p, std::vector<int>& cell_off, std::vector<int
 void build_twiddles(int N, std::vector<float2>& tw);
 
 // api.cu helpers used by the kernels' launch code
+// Let kernel `fn` take as much dynamic shared memory as the device allows (its
+// static shared memory subtracted).  Kernels are shared by every plan, so this
+// limit is never set to one plan's need: a plan created later must not shrink
+// what the launches of an earlier plan ask for.
+cudaError_t allow_max_smem(const void* fn, int optin);
 void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s);
 void ev_end(epic_plan_s* p, cudaStream_t s);
 epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);

@@ -40,7 +40,7 @@ namespace epic {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr size_t kScratchBudget = 96ull << 20;  // grid tiles of one (channel group, time chunk)
+constexpr size_t kScratchBudget = 192ull << 20;  // grid tiles of one (channel group, time chunk)
 constexpr long long kWaitBudget = 4000000000LL;  // clock cycles before a wait gives up (~2 s)
 constexpr int kGridFramesPerBlock = 8;            // frames gridded per block (cell lists read once)
 
@@ -2038,7 +2038,7 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F)
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_ps)");
     if (bytes + fa.sharedSizeBytes > (size_t)p->smem_optin) return EPIC_ERR_UNSUPPORTED;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = allow_max_smem(fn, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_ps)");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, bytes);
@@ -2063,7 +2063,7 @@ static epic_status grid_bal_config(epic_plan_s* p, int F)
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_bal)");
     if (bytes + fa.sharedSizeBytes > (size_t)p->smem_optin) return EPIC_ERR_UNSUPPORTED;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = allow_max_smem(fn, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_bal)");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridBalThreads, bytes);
@@ -2414,7 +2414,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
     }
 #define EPIC_GRID_ATTR(CS, FF)                                                                                      \
     if (e == cudaSuccess)                                                                                           \
-        e = cudaFuncSetAttribute(k_dftgemm_grid<CS, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_optin);
+        e = allow_max_smem((const void*)k_dftgemm_grid<CS, FF>, p->smem_optin);
     e = cudaSuccess;
     EPIC_GRID_ATTR(true, 4)
     EPIC_GRID_ATTR(true, 2)
@@ -2424,13 +2424,13 @@ epic_status dftgemm_setup(epic_plan_s* p)
     EPIC_GRID_ATTR(false, 1)
 #undef EPIC_GRID_ATTR
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
-    e = cudaFuncSetAttribute(k_dftgemm_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_ws2<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_ws3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    e = allow_max_smem((const void*)k_dftgemm_ws<0>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws2<0>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0>, p->smem_optin);
     p->tc.ws_variant = p->tc.ws ? 3 : 0;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma_fast<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dftgemm_mma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->tc.smem);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma_fast<0>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma<1>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma<2>, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_mma)");
     return EPIC_OK;
 }

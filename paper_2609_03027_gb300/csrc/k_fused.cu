@@ -202,8 +202,7 @@ epic_status fused_setup(epic_plan_s* p)
     p->time_chunk = p->max_time;
     cudaError_t e = cudaSuccess;
 #define EPIC_FUSED_ATTR(n)                                                                                      \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_fp32<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                   p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_fused_fp32<n>, p->smem_optin);
     EPIC_FUSED_ATTR(1)
     EPIC_FUSED_ATTR(2)
     EPIC_FUSED_ATTR(4)

@@ -172,12 +172,12 @@ epic_status plain_setup(epic_plan_s* p)
             p->last_error = "plain path: frame of A*P voltages does not fit in shared memory";
             return EPIC_ERR_UNSUPPORTED;
         }
-        e = cudaFuncSetAttribute(k_plain_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sg);
+        e = allow_max_smem((const void*)k_plain_grid, p->smem_optin);
         if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_plain_grid)");
     }
-    e = cudaFuncSetAttribute(k_plain_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(p->N));
+    e = allow_max_smem((const void*)k_plain_fft_rows, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_plain_fft_rows)");
-    e = cudaFuncSetAttribute(k_plain_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem(p->N));
+    e = allow_max_smem((const void*)k_plain_fft_cols, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_plain_fft_cols)");
     return EPIC_OK;
 }

@@ -120,3 +120,19 @@ def test_set_param_values_match_oracle(path, name, values):
         for val in values:
             plan.set_param(name, val)
             assert_parity(plan.image(v).cpu().numpy(), ref, path, f"{name}={val}")
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_plan_created_later_does_not_break_earlier_plan(path):
+    # kernels are shared by all plans: a later plan with smaller boxes must not
+    # lower the shared-memory limit the earlier plan's launches need
+    big = _cfg(n_ant=120, n_chan=3, grid_n=128, gcf_k=7, n_time=20, seed=45, diameter_m=40.0)
+    small = _cfg(n_ant=10, n_chan=2, grid_n=16, gcf_k=3, n_time=20, seed=46, diameter_m=4.0)
+    vb, vs = synth.make_voltages(big), synth.make_voltages(small)
+    with E.Plan.from_config(big, path=path) as pb, E.Plan.from_config(small, path=path) as ps:
+        ob = pb.image(torch.from_numpy(vb).cuda()).cpu().numpy()
+        os_ = ps.image(torch.from_numpy(vs).cuda()).cpu().numpy()
+        pb.sync()
+        ps.sync()
+    assert_parity(ob, oracle_image(big, vb), path, "earlier plan")
+    assert_parity(os_, oracle_image(small, vs), path, "later plan")
