@@ -223,18 +223,21 @@ def run_reference(args, cfg, world, rank):
 
 # ----------------------------------------------------------------------------- traffic record
 
-def recorded_traffic(kernel: str, workload: int):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+def recorded_traffic(kernel: str, workload: int, samples: int):
+    """DRAM bytes of one launch processing `samples` time samples, from the committed ncu
+    summary (profiles/traffic.json: bytes per sample of one capture), if the kernel source
+    is unchanged since the capture; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get(f"{kernel}@cfg{workload}")
+    key = "k_dftgemm_grid" if kernel.startswith("k_dftgemm_grid") else kernel
+    rec = json.load(open(path)).get(f"{key}@cfg{workload}")
     if not rec:
         return None
     src = os.path.join(ROOT, "paper_2609_03027_gb300", "csrc", rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha"]:
         return None
-    return float(rec["bytes_per_launch"])
+    return float(rec["bytes_per_sample"]) * samples
 
 
 def run_e2e(E, cfg, volt, out, T, units, world, dev, args, tuning=None):
@@ -443,7 +446,8 @@ def main():
         achieved = algo_step / (kstep_ms / 1e3) / 1e9
         peak, unit = pk["hbm_gbs"], "GB/s"
     roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": recorded_traffic(dom, args.config),
+            "frac": achieved / peak,
+            "traffic": recorded_traffic(dom, args.config, int(round(T / per_step_launches))),
             "peak_source": pk["source"] if bound != "alu" else "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
             "kernel_ms": kavg_ms, "launches_per_step": per_step_launches,
             "kernel_share": sum(ktimes[dom]) / sum(sum(v) for v in ktimes.values())}
