@@ -176,6 +176,8 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  *   FUSED_FP32    slab         image columns per work item
  *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
  *                              control warp does (when the occupied box allows either);
+ *                 split        work of the control-warp kernel: -1 automatic, 0 whole work
+ *                              items per SM, 1 equal (item, time sample) shares per SM;
  *                 grid_kernel  gridding kernel: 1 row-major cell walk, 2 cells in lists sorted
  *                              by length (Gaussian GCF, when its tiles fit in shared memory);
  *                 grid_frames  frames per pass of the gridding kernel;
@@ -243,7 +245,9 @@ epic_status epic_image_static_scratch(epic_plan_t plan, const uint8_t* volt, int
  * Images go to caller-owned device accumulators (use EPIC_ACCUMULATE to continue
  * an integration across blocks).  Latency of a block = wall time from submission
  * to completion of its kernels.  A plan given to a server must not be used by
- * other epic_image calls until its blocks are done.
+ * other epic_image calls until its blocks are done.  The server's streams do not
+ * wait for work the caller queued on other streams: the accumulators must be
+ * complete (e.g. the caller's stream synchronised) when a block is submitted.
  * ------------------------------------------------------------------------- */
 typedef struct epic_server_s* epic_server_t;
 

@@ -57,6 +57,8 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.a1p);
     cudaFree(p->tc.a1p_off);
     cudaFree(p->tc.gtask);
+    cudaFree(p->tc.partial);
+    cudaFree(p->tc.counters);
     cudaFree(p->tc.gtask_off);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);

@@ -67,6 +67,9 @@ struct TcState {
     uint16_t* a1p = nullptr;       // stage-1 operands per (channel, 64-column kx pair)
     long long* a1p_off = nullptr;
     int n_gp = 0;                  // 64-column pairs per channel
+    float* partial = nullptr;      // k_dftgemm_ws3: partial sums of items split between blocks
+    int* counters = nullptr;       // k_dftgemm_ws3: per item, parts stored so far
+    int split = -1;                // k_dftgemm_ws3 work split: -1 auto, 0 whole items, 1 equal shares
 };
 
 struct KernelEvent {
@@ -165,5 +168,6 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F);
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant);
 epic_status dftgemm_set_grid_kernel(epic_plan_s* p, int variant);
+epic_status dftgemm_set_split(epic_plan_s* p, int mode);
 
 }  // namespace epic

@@ -104,6 +104,8 @@ struct MmaArgs {
     // warp-specialised variant only
     const uint16_t* a1p;        // stage-1 operands per (channel, 64-column kx pair)
     const long long* a1p_off;
+    float* partial;             // k_dftgemm_ws3: 2 slots per block of 4 x 128 x 64 partial sums
+    int* counters;              // k_dftgemm_ws3: per item, blocks that stored a part (reset by the last)
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -1764,19 +1766,77 @@ __global__ void __launch_bounds__(kWs2Threads, 1) k_dftgemm_ws2(MmaArgs a)
 //     wait d2_full(t-1) -> epilogue 2 (t-1) -> arrive d2_empty
 // Items are separated by two block-wide named barriers (operands loaded; item done).
 constexpr int kWs3Threads = 640;
+constexpr int kWs3MaxBlocks = 256;  // blocks per launch (one per SM) the split bookkeeping holds
 
 __device__ __forceinline__ void bar_all(int id)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWs3Threads) : "memory");
 }
 
-template <int dummy>
+// A split work item (k_dftgemm_ws3, equal shares) after this block stored its part
+// to its slot: the block that stores the item's last part -- counted on the item's
+// counter -- adds all parts in block order and writes (or adds) the images.  Kept
+// out of line so that the frame loop's register allocation does not carry it.
+__device__ __noinline__ void ws3_split_finish(const MmaArgs& a, int item, int c, int ky, int kx0, size_t px,
+                                              long long U, int tid, int* split_slot, int* split_n)
+{
+    __threadfence();
+    asm volatile("bar.sync 3, 512;" ::: "memory");
+    if (tid == 0) {
+        const long long s0 = (long long)item * a.nt, s1 = s0 + a.nt - 1;
+        const long long G = gridDim.x;
+        auto owner = [&](long long f) {  // block whose range [U b / G, U (b + 1) / G) holds f
+            long long b = f * G / U;
+            while (b + 1 < G && U * (b + 1) / G <= f) ++b;
+            while (b > 0 && U * b / G > f) --b;
+            return (int)b;
+        };
+        int n = 0;
+        const int b1 = owner(s1);
+        for (int b = owner(s0); b <= b1; ++b) {
+            const long long bw0 = U * b / G;
+            if (bw0 == U * (b + 1) / G) continue;  // no frames: no part
+            split_slot[n++] = 2 * b + (s0 <= bw0 ? 0 : 1);
+        }
+        const bool last = atomicAdd(&a.counters[item], 1) == n - 1;
+        if (last) a.counters[item] = 0;  // ready for the next launch
+        *split_n = last ? n : 0;
+    }
+    asm volatile("bar.sync 3, 512;" ::: "memory");
+    const int n = *split_n;
+    if (n > 0 && ky < a.N && kx0 < a.N) {
+        __threadfence();
+        const size_t NN = (size_t)a.N * a.N;
+        const int nk = min(16, a.N - kx0);
+        for (int pr = 0; pr < a.nprod; ++pr) {  // one product at a time: 16 live sums
+            float sum[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sum[i] = 0.f;
+            for (int k = 0; k < n; ++k) {
+                const float* q = a.partial + ((size_t)split_slot[k] * 4 + pr) * 8192 + px;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) {
+                    const float4 u = __ldcg(reinterpret_cast<const float4*>(q + i));
+                    sum[i] += u.x;
+                    sum[i + 1] += u.y;
+                    sum[i + 2] += u.z;
+                    sum[i + 3] += u.w;
+                }
+            }
+            store_pixels16(a.out + ((size_t)c * a.nprod + pr) * NN + (size_t)ky * a.N + kx0, nk, a.accumulate, sum);
+        }
+    }
+}
+
+template <int SPLIT>
 __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar_a, d1_full[2], b2_full[2], d2_full, d2_empty, tile_full[2];
     __shared__ uint32_t tmem_sh;
     __shared__ int err_sh;
+    __shared__ int split_slot[kWs3MaxBlocks];  // partial slots of a split item, in block order
+    __shared__ int split_n;                    // > 0: this block completes the item; sum split_n slots
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         tc::tmem_alloc(&tmem_sh, 512);
@@ -1804,22 +1864,40 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
     const int R2 = 2 * 64 * P;
     const uint32_t a2col = 2u * a.d1_cols;
     const int items = a.n_ch * a.n_kb * a.n_g;
+    // this block's share of the launch.  split: the (item, frame) pairs [wb0, wb1) in
+    // item-major order (equal shares; items cut at share boundaries are summed by the
+    // block that stores their last part); else whole items blockIdx.x, + gridDim.x, ...
+    const long long U = (long long)items * a.nt;
+    const long long wb0 = U * blockIdx.x / gridDim.x, wb1 = U * (blockIdx.x + 1) / gridDim.x;
 
     if (warp >= 16) {
         // ------------------------------------------------------------ control warpgroup
         asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
         uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
         const bool boss = warp == 16 && lane == 0;
-        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        long long w = wb0;
+        for (int it = 0;; ++it) {
+            int item, fs, nt;  // work item, its first frame and the frames of this segment
+            if (SPLIT) {
+                if (w >= wb1) break;
+                item = (int)(w / a.nt);
+                fs = (int)(w % a.nt);
+                nt = (int)min((long long)(a.nt - fs), wb1 - w);
+                w += nt;
+            } else {
+                item = blockIdx.x + it * gridDim.x;
+                if (item >= items) break;
+                fs = 0;
+                nt = a.nt;
+            }
             const int g = item % a.n_g, cl = item / (a.n_g * a.n_kb);
             const int c = a.c0 + cl;
             const int4 bx = a.box[c];
             const int nxp = bx.z, nyp = bx.w;
             const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
-            const int nt = a.nt;
             const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
-            const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride;
             const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
+            const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride + (size_t)fs * frame_step;
             if (boss) {
                 const uint32_t a1_bytes = 256u * pad64(K1);
                 tc::mbar_expect_tx(&bar_a, a1_bytes);
@@ -1887,13 +1965,27 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         const int q4 = warp & 3, j4 = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
         const int h2 = j4 >> 1;
-        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        long long w = wb0;
+        for (int it = 0;; ++it) {
+            int item, fs, nt;  // work item, its first frame and the frames of this segment
+            if (SPLIT) {
+                if (w >= wb1) break;
+                item = (int)(w / a.nt);
+                fs = (int)(w % a.nt);
+                nt = (int)min((long long)(a.nt - fs), wb1 - w);
+                w += nt;
+            } else {
+                item = blockIdx.x + it * gridDim.x;
+                if (item >= items) break;
+                fs = 0;
+                nt = a.nt;
+            }
+            const bool first_seg = it == 0;
             const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
             const int c = a.c0 + cl;
             const int4 bx = a.box[c];
             const int nyp = bx.w;
             const int K2 = 2 * nyp;
-            const int nt = a.nt;
             if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
                 const uint32_t* src =
                     a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
@@ -1966,10 +2058,21 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             bar_all(2);
             tc::fence_after_sync();
             if (err_sh) break;
-            // images: row ky = 128 kb + 32 q4 + lane, 16 kx from 64 g + 32 h2 + 16 (j4 & 1)
+            // images: row ky = 128 kb + 32 q4 + lane, 16 kx from 64 g + 32 h2 + 16 (j4 & 1); a
+            // segment that is only part of its item goes to this block's partial slot
             const int ky = 128 * kb + 32 * q4 + lane;
             const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
-            if (ky < a.N && kx0 < a.N) {
+            if (SPLIT && (fs != 0 || nt != a.nt)) {
+                const size_t px = (size_t)(32 * q4 + lane) * 64 + 32 * h2 + 16 * (j4 & 1);
+                float* o = a.partial + (2 * (size_t)blockIdx.x + (first_seg ? 0 : 1)) * 4 * 8192 + px;
+                store_pixels16(o, 16, 0, axx);
+                if (a.nprod == 4) {
+                    store_pixels16(o + 8192, 16, 0, ayy);
+                    store_pixels16(o + 2 * 8192, 16, 0, arx);
+                    store_pixels16(o + 3 * 8192, 16, 0, aix);
+                }
+                ws3_split_finish(a, item, c, ky, kx0, px, U, tid, split_slot, &split_n);
+            } else if (ky < a.N && kx0 < a.N) {
                 const size_t NN = (size_t)a.N * a.N;
                 float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
                 const int nk = min(16, a.N - kx0);
@@ -1988,6 +2091,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
     if (err_sh && tid == 0) atomicExch(a.status, 1);
 }
 
+
 }  // namespace
 
 // Time samples per chunk so that the grid tiles of one (channel group, time
@@ -1996,6 +2100,15 @@ epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 {
     if (!p->tc.ws || variant < 1 || variant > 3) return EPIC_ERR_UNSUPPORTED;
     p->tc.ws_variant = variant;
+    return EPIC_OK;
+}
+
+// Work split of k_dftgemm_ws3: -1 = automatic (equal shares when a launch has fewer
+// items than SMs), 0 = whole items per block, 1 = equal (item, frame) shares.
+epic_status dftgemm_set_split(epic_plan_s* p, int mode)
+{
+    if (!p->tc.ws || mode < -1 || mode > 1) return EPIC_ERR_UNSUPPORTED;
+    p->tc.split = mode;
     return EPIC_OK;
 }
 
@@ -2381,15 +2494,24 @@ epic_status dftgemm_setup(epic_plan_s* p)
                                                  cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(p, e, "gridding task lists upload");
             p->tc.gtask_max = tmax;
-            p->dt.dft_bytes += tasks.size() * sizeof(int2) + toff.size() * sizeof(int);
             const int keep_f = p->tc.grid_frames;
             p->tc.grid_variant = 2;
             epic_status bst = EPIC_ERR_UNSUPPORTED;
             for (int gf = 2; gf >= 1 && bst == EPIC_ERR_UNSUPPORTED; gf >>= 1) bst = grid_bal_config(p, gf);
-            if (bst != EPIC_OK) {
+            if (bst != EPIC_OK) {  // the balanced kernel does not fit: keep the row-major one
                 if (bst != EPIC_ERR_UNSUPPORTED) return bst;
                 p->tc.grid_variant = 1;
-                if (p->tc.grid_ps) dftgemm_grid_config(p, keep_f);
+                cudaFree(p->tc.gtask);
+                cudaFree(p->tc.gtask_off);
+                p->tc.gtask = nullptr;
+                p->tc.gtask_off = nullptr;
+                p->tc.gtask_max = 0;
+                if (p->tc.grid_ps) {
+                    const epic_status kst = dftgemm_grid_config(p, keep_f);
+                    if (kst != EPIC_OK) return kst;
+                }
+            } else {
+                p->dt.dft_bytes += tasks.size() * sizeof(int2) + toff.size() * sizeof(int);
             }
         }
     }
@@ -2427,7 +2549,17 @@ epic_status dftgemm_setup(epic_plan_s* p)
     e = allow_max_smem((const void*)k_dftgemm_ws<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws2<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1>, p->smem_optin);
     p->tc.ws_variant = p->tc.ws ? 3 : 0;
+    if (p->tc.ws && p->sm_count > kWs3MaxBlocks) p->tc.ws_variant = 1;
+    if (p->tc.ws && e == cudaSuccess) {
+        const size_t n_items = (size_t)p->tc.cg * n_kb * n_gp;
+        e = cudaMalloc(&p->tc.partial, (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&p->tc.counters, n_items * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->tc.counters, 0, n_items * sizeof(int));
+        if (e == cudaSuccess)
+            p->dt.dft_bytes += (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float) + n_items * sizeof(int);
+    }
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma_fast<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma<1>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_mma<2>, p->smem_optin);
@@ -2549,7 +2681,14 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                                  : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
             if (p->tc.ws) {
                 a.n_g = p->tc.n_gp;
-                if (p->tc.ws_variant == 3) k_dftgemm_ws3<0><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                if (p->tc.ws_variant == 3) {
+                    a.partial = p->tc.partial;
+                    a.counters = p->tc.counters;
+                    if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
+                        k_dftgemm_ws3<1><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a);
+                    else
+                        k_dftgemm_ws3<0><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                }
                 else if (p->tc.ws_variant == 2) k_dftgemm_ws2<0><<<grid, kWs2Threads, p->tc.smem, s>>>(a);
                 else k_dftgemm_ws<0><<<grid, kWsThreads, p->tc.smem, s>>>(a);
             } else if (p->tc.fast) k_dftgemm_mma_fast<0><<<grid, kMmaThreads, p->tc.smem, s>>>(a);

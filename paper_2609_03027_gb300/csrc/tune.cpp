@@ -22,6 +22,7 @@ epic_status set_dft_frames(epic_plan_s* p, int f) { return epic::dftgemm_grid_co
 epic_status set_fused_slab(epic_plan_s* p, int sw) { return epic::fused_set_slab(p, sw); }
 epic_status set_dft_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_kernel(p, v); }
 epic_status set_dft_grid_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_grid_kernel(p, v); }
+epic_status set_dft_split(epic_plan_s* p, int v) { return epic::dftgemm_set_split(p, v); }
 
 // the tuning parameters of a plan's path with their candidate and current values
 std::vector<Knob> knobs_for(const epic_plan_s* p)
@@ -34,11 +35,12 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
         knobs.push_back({"slab", {8, 16, 32}, p->slab, set_fused_slab});
     } else if (p->path == EPIC_PATH_DFTGEMM_FP16) {
         if (p->tc.ws) knobs.push_back({"mma_kernel", {1, 2, 3}, p->tc.ws_variant, set_dft_kernel});
+        if (p->tc.ws) knobs.push_back({"split", {-1, 0, 1}, p->tc.split, set_dft_split});
         if (p->tc.grid_ps && p->tc.gtask)
             knobs.push_back({"grid_kernel", {1, 2}, p->tc.grid_variant, set_dft_grid_kernel});
         if (p->tc.grid_ps || p->tc.gtask)
             knobs.push_back({"grid_frames", {1, 2, 4, 8}, p->tc.grid_frames, set_dft_frames});
-        knobs.push_back({"chunk_mb", {24, 48, 96, 192}, budget_mb, set_dft_chunk});
+        knobs.push_back({"chunk_mb", {48, 96, 192, 384, 768}, budget_mb, set_dft_chunk});
     }
     return knobs;
 }

@@ -164,3 +164,16 @@ def test_invalid_calls_fail_before_launch(path):
         assert L.epic_image(plan._h, v.ctypes.data, 4, None, out.data_ptr(), 0) == 1      # host pointer
         assert L.epic_image(plan._h, d.data_ptr(), 4, None, out.data_ptr(), 8) == 1       # unknown flag
         plan.sync()
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_one_plan_many_block_lengths(path):
+    # the same plan images blocks of many lengths in a row (the tensor path splits
+    # the (item, frame) pairs of a launch over the SMs differently for each length)
+    cfg = synth.small_config(n_ant=30, n_chan=3, n_pol=2, grid_n=32, gcf_k=3, n_time=40, seed=27)
+    v = synth.make_voltages(cfg)
+    d = torch.from_numpy(v).cuda()
+    with E.Plan.from_config(cfg, path=path) as plan:
+        for T in (1, 8, 3, 40, 13, 2, 29):
+            got = plan.image(d[:T].contiguous()).cpu().numpy()
+            assert_parity(got, oracle_image(cfg, v[:T]), path, f"T={T}")

@@ -46,6 +46,7 @@ def test_each_block_same_alone_and_in_the_mix():
     # in the mix: all submitted at once, different stations overlap on the device
     outs = [torch.full((stations[si][0].n_chan, stations[si][0].n_prod, stations[si][0].grid_n,
                         stations[si][0].grid_n), -1.0, device="cuda") for si, _ in blocks]
+    torch.cuda.synchronize()                  # the server's streams do not wait for torch's
     with E.Server(device_bytes=64 << 20, slots=4) as srv:
         tickets = []
         for (si, v), o in zip(blocks, outs):
@@ -73,6 +74,7 @@ def test_integration_continues_across_blocks():
     for b, v in enumerate(vs):
         plan.image(torch.from_numpy(v).cuda(), out=ref, accumulate=b > 0)
     acc = torch.full_like(ref, 5.0)
+    torch.cuda.synchronize()                  # the server's streams do not wait for torch's
     with E.Server(device_bytes=32 << 20, slots=2) as srv:
         ts = [srv.submit(plan, v, acc, accumulate=b > 0) for b, v in enumerate(vs)]
         for t in ts:
