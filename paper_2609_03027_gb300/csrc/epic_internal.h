@@ -57,6 +57,9 @@ struct TcState {
     int2* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list
+    int2* gell = nullptr;          // balanced gridding: interleaved (element, weight) entries
+    int* gell_off = nullptr;       // [C + 1]
+    int gell_max = 0;              // largest entry list (with padding)
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2
     uint32_t* a2w = nullptr;       // stage-2 operand rows as packed FP16 pairs (fast variant)
     long long* a2w_off = nullptr;

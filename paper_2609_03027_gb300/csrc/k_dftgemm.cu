@@ -81,6 +81,13 @@ __host__ __device__ inline int pad64(int k) { return (k + 63) & ~63; }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+inline int __float_as_int_host(float f)
+{
+    int i;
+    std::memcpy(&i, &f, sizeof i);
+    return i;
+}
+
 // ------------------------------------------------------------------ device
 struct MmaArgs {
     const uint8_t* tiles;
@@ -472,14 +479,19 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
 // the F frames of a pass are assembled in shared-memory tiles that the TMA
 // engine then stores with one bulk copy per frame.  Tile buffers are double
 // buffered across passes; cells no task touches stay zero from the channel's
-// first pass.
+// first pass.  The (element, weight) entries of the 32 cells a warp handles together
+// are interleaved (entry k of lane l at 32 k + l), so a warp reads them as one
+// contiguous 256-byte row per step.
 constexpr int kGridBalThreads = 512;
 
 struct GridBalArgs {
     GridArgs g;
-    const int2* tasks;      // per channel: (cell | count << 24, first entry) sorted by count
+    const int2* tasks;      // per channel: (cell | group's longest list << 24, group's first entry)
     const int* task_off;    // [C + 1]
+    const int2* ell;        // per channel: (element, weight bits), 32 lanes interleaved per group
+    const int* ell_off;     // [C + 1]
     int max_tasks;          // largest task count of a channel
+    int max_ell;            // largest entry count of a channel (with padding)
     unsigned tile_max;      // shared-memory bytes per tile (largest channel)
 };
 
@@ -512,7 +524,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
     const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
     uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
     int2* stask = reinterpret_cast<int2*>(stile + 2ull * F * ba.tile_max);
-    int2* con = stask + ba.max_tasks;
+    int2* sell = stask + ba.max_tasks;
 
     const long long W = (long long)a.n_ch * a.nt;
     const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
@@ -562,11 +574,8 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
             const int t0 = ba.task_off[c];
             ntask = ba.task_off[c + 1] - t0;
             for (int i = tid; i < ntask; i += blockDim.x) stask[i] = ba.tasks[t0 + i];
-            const int* gptr = a.cell_ptr + a.cell_off[c];
-            const int base = gptr[0];
-            const int ncon = gptr[nxp * nyp] - base;
-            for (int i = tid; i < ncon; i += blockDim.x)
-                con[i] = make_int2(a.ce[base + i], __float_as_int(a.cw[base + i].x));
+            const int e0 = ba.ell_off[c], nell = ba.ell_off[c + 1] - e0;
+            for (int i = tid; i < nell; i += blockDim.x) sell[i] = ba.ell[e0 + i];
             staged = cl;
         }
         if (a.bulk) {
@@ -605,8 +614,9 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
             float4 g[F];
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int q = tk.y; q < tk.y + n; ++q) {
-                const int2 cr = con[q];
+            const int2* lst = sell + tk.y + (s & 31);
+            for (int k = 0; k < n; ++k) {
+                const int2 cr = lst[32 * k];
                 const float wv = __int_as_float(cr.y);
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) {
@@ -2168,8 +2178,7 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F)
 static epic_status grid_bal_config(epic_plan_s* p, int F)
 {
     if (!p->tc.gtask || (F != 1 && F != 2 && F != 4)) return EPIC_ERR_UNSUPPORTED;
-    const size_t bytes =
-        grid_bal_smem(F, p->A, p->P, p->tc.gtask_max, p->tc.grid_max_list, (unsigned)p->tc.stride);
+    const size_t bytes = grid_bal_smem(F, p->A, p->P, p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride);
     const void* fn = F == 4 ? (const void*)k_dftgemm_grid_bal<4>
                    : F == 2 ? (const void*)k_dftgemm_grid_bal<2> : (const void*)k_dftgemm_grid_bal<1>;
     cudaFuncAttributes fa{};
@@ -2464,12 +2473,16 @@ epic_status dftgemm_setup(epic_plan_s* p)
         std::vector<int> coff, cptr, ce;
         std::vector<float2> cw;
         build_csr(p, coff, cptr, ce, cw);
-        std::vector<int2> tasks;
-        std::vector<int> toff(C + 1, 0);
+        // Cells of a channel sorted by contribution count; groups of 32 consecutive cells
+        // (the lanes of one warp) store their (element, weight) entries interleaved, entry k
+        // of lane l at 32 k + l, padded with zero weights to the group's longest list.
+        std::vector<int2> tasks, ell;
+        std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
         bool fits = true;
-        int tmax = 0;
+        int tmax = 0, emax = 0;
         for (int c = 0; c < C && fits; ++c) {
             toff[c] = (int)tasks.size();
+            eoff[c] = (int)ell.size();
             const int* ptr = &cptr[coff[c]];
             const int ncell = p->box[c].nx * p->box[c].ny;
             std::vector<int> idx;
@@ -2477,14 +2490,32 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 if (ptr[r + 1] > ptr[r]) idx.push_back(r);
             std::stable_sort(idx.begin(), idx.end(),
                              [&](int u, int v) { return ptr[u + 1] - ptr[u] > ptr[v + 1] - ptr[v]; });
-            for (int r : idx) {
-                const int n = ptr[r + 1] - ptr[r];
-                if (n > 255 || r >= (1 << 24)) fits = false;
-                tasks.push_back(make_int2(r | (n << 24), ptr[r] - ptr[0]));
+            for (size_t g0 = 0; g0 < idx.size(); g0 += 32) {
+                const int members = (int)std::min<size_t>(32, idx.size() - g0);
+                const int nmax = ptr[idx[g0] + 1] - ptr[idx[g0]];
+                const int base = (int)ell.size() - eoff[c];
+                if (nmax > 255) fits = false;
+                for (int k = 0; k < nmax; ++k)
+                    for (int l = 0; l < 32; ++l) {
+                        int2 en = make_int2(0, __float_as_int_host(0.f));
+                        if (l < members) {
+                            const int r = idx[g0 + l];
+                            if (k < ptr[r + 1] - ptr[r])
+                                en = make_int2(ce[ptr[r] + k], __float_as_int_host(cw[ptr[r] + k].x));
+                        }
+                        ell.push_back(en);
+                    }
+                for (int l = 0; l < members; ++l) {
+                    const int r = idx[g0 + l];
+                    if (r >= (1 << 24)) fits = false;
+                    tasks.push_back(make_int2(r | (nmax << 24), base));
+                }
             }
             tmax = std::max(tmax, (int)idx.size());
+            emax = std::max(emax, (int)ell.size() - eoff[c]);
         }
         toff[C] = (int)tasks.size();
+        eoff[C] = (int)ell.size();
         if (fits && !tasks.empty()) {
             e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int2));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int2),
@@ -2492,8 +2523,15 @@ epic_status dftgemm_setup(epic_plan_s* p)
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gtask_off, toff.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask_off, toff.data(), toff.size() * sizeof(int),
                                                  cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell, ell.size() * sizeof(int2));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell, ell.data(), ell.size() * sizeof(int2),
+                                                 cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_off, eoff.size() * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_off, eoff.data(), eoff.size() * sizeof(int),
+                                                 cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(p, e, "gridding task lists upload");
             p->tc.gtask_max = tmax;
+            p->tc.gell_max = emax;
             const int keep_f = p->tc.grid_frames;
             p->tc.grid_variant = 2;
             epic_status bst = EPIC_ERR_UNSUPPORTED;
@@ -2503,15 +2541,19 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 p->tc.grid_variant = 1;
                 cudaFree(p->tc.gtask);
                 cudaFree(p->tc.gtask_off);
+                cudaFree(p->tc.gell);
+                cudaFree(p->tc.gell_off);
                 p->tc.gtask = nullptr;
                 p->tc.gtask_off = nullptr;
+                p->tc.gell = nullptr;
+                p->tc.gell_off = nullptr;
                 p->tc.gtask_max = 0;
                 if (p->tc.grid_ps) {
                     const epic_status kst = dftgemm_grid_config(p, keep_f);
                     if (kst != EPIC_OK) return kst;
                 }
             } else {
-                p->dt.dft_bytes += tasks.size() * sizeof(int2) + toff.size() * sizeof(int);
+                p->dt.dft_bytes += (tasks.size() + ell.size()) * sizeof(int2) + (toff.size() + eoff.size()) * sizeof(int);
             }
         }
     }
@@ -2632,7 +2674,10 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     ba.g = g;
                     ba.tasks = p->tc.gtask;
                     ba.task_off = p->tc.gtask_off;
+                    ba.ell = p->tc.gell;
+                    ba.ell_off = p->tc.gell_off;
                     ba.max_tasks = p->tc.gtask_max;
+                    ba.max_ell = p->tc.gell_max;
                     ba.tile_max = (unsigned)p->tc.stride;
                     if (F == 4) k_dftgemm_grid_bal<4><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
                     else if (F == 2) k_dftgemm_grid_bal<2><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
