@@ -44,6 +44,7 @@ WORKLOADS = {
     2: "lwa-station: 256 dual-pol el in 100x110 m ellipse, 128 ch x 25 kHz @ 56 MHz, 128x128 grid, 5x5 GCF, T=1000",
     3: "skalow-station: 256 dual-pol el in 38 m disc, 384 ch 50-350 MHz, 128x128 grid, 7x7 freq-scaled GCF, T=512",
     4: "dense-4096: 64x64 jittered lattice dual-pol, 64 ch from 150 MHz, 256x256 grid, 3x3 GCF, T=256",
+    6: "large-grid: 20000 dual-pol el in 240 m disc, 1 x 781.25 kHz ch @ 159 MHz, 512x512 grid, 2x2 GCF, T=1000",
 }
 
 
@@ -350,7 +351,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="epic", choices=["epic", "reference"])
     ap.add_argument("--path", default="dftgemm", choices=["plain", "fused", "dftgemm", "auto"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 6])
     ap.add_argument("--compare", default="plain", help="also time this path (comma list, '' for none)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-time", type=int, default=250, help="time samples per reference step")

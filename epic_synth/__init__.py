@@ -117,7 +117,7 @@ def _sky_uniform_box(rng, n, half, amps):
 
 
 def config(idx: int) -> EpicConfig:
-    """The four fixed imaging workloads (1..4)."""
+    """The fixed imaging workloads: 1..4, and 6 (a 512x512 grid; 5 is the streaming mix)."""
     if idx == 1:
         # 64 elements in a 20 m disc, lambda = 2 m, 1 pol, 4 channels, 32x32 grid,
         # 3x3 Gaussian GCF with sigma 0.5 cell, 256 samples, one source at (0.2, -0.1).
@@ -160,6 +160,17 @@ def config(idx: int) -> EpicConfig:
         flux = 10.0 ** rng.uniform(-2.0, 0.0, size=n)
         return EpicConfig("dense-4096el-256grid", pos, f, 2, 256, 3, 0.5, 150e6, False, 256,
                           lm, np.sqrt(flux), 2.0, 4)
+    if idx == 6:
+        # Large-grid station (the paper's second prototype scale): 20,000 dual-pol elements
+        # uniform in a 240 m disc, one 781.25 kHz coarse channel at 159 MHz, 512x512 grid
+        # (the aperture fills about half of it at lambda/2 spacing), 2x2 Gaussian GCF,
+        # 1000 samples, 3 sources.
+        rng = np.random.default_rng([6, 1_000_000])
+        pos = layout_disc(20000, 240.0, rng)
+        f = np.array([159e6 + 390.625e3])
+        lm, amp = _sky_uniform_box(rng, 3, 0.5, [0.5, 0.35, 0.25])
+        return EpicConfig("proto2-20000el-512grid", pos, f, 2, 512, 2, 0.5, float(f[0]), False, 1000,
+                          lm, amp, 2.0, 6)
     raise ValueError(f"no such config {idx}")
 
 

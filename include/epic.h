@@ -97,7 +97,7 @@ typedef struct {
     int n_chan;             /* channels C >= 1                                                    */
     const double* freq_hz;  /* host [n_chan] centre frequency of each channel, > 0                */
     const double* cell_m;   /* host [n_chan] grid spacing Delta_c, or NULL for lambda_c / 2       */
-    int grid_n;             /* N: power of two, 8..256                                            */
+    int grid_n;             /* N: power of two, 8..512                                            */
     epic_gcf_desc gcf;
     int path;               /* epic_path                                                          */
     int max_time;           /* largest T of one call (sizes scratch and host staging), >= 1       */

@@ -192,7 +192,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     if (d->n_ant < 1 || !d->pos_m) return bad("n_ant must be >= 1 and pos_m non-NULL");
     if (d->n_pol != 1 && d->n_pol != 2) return bad("n_pol must be 1 or 2");
     if (d->n_chan < 1 || !d->freq_hz) return bad("n_chan must be >= 1 and freq_hz non-NULL");
-    if (!is_pow2(d->grid_n) || d->grid_n < 8 || d->grid_n > 256) return bad("grid_n must be a power of two in 8..256");
+    if (!is_pow2(d->grid_n) || d->grid_n < 8 || d->grid_n > 512) return bad("grid_n must be a power of two in 8..512");
     if (d->max_time < 1) return bad("max_time must be >= 1");
     if (d->gcf.K < 1 || d->gcf.K > 8 || d->gcf.K > d->grid_n) return bad("gcf.K must be in 1..8");
     if (d->gcf.kind == EPIC_GCF_GAUSSIAN) {

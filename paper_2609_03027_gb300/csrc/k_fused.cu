@@ -190,7 +190,7 @@ epic_status fused_set_slab(epic_plan_s* p, int SW)
 epic_status fused_setup(epic_plan_s* p)
 {
     const int N = p->N;
-    const int SW = N >= 256 ? 16 : std::min(32, N);
+    const int SW = N >= 512 ? 8 : N >= 256 ? 16 : std::min(32, N);  // at most 16 pixels per thread
     const size_t bytes =
         sizeof(float2) * fused_smem_elems(N, p->A, p->P, SW, p->box_max_x, p->box_max_y);
     if ((int)bytes > p->smem_optin) {

@@ -55,6 +55,41 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid(const uint8_t* __restri
     }
 }
 
+// Same as k_plain_grid for frames whose A*P voltages do not fit in shared memory
+// (very large arrays): each contribution reads and unpacks its voltage byte
+// through the read-only data cache.
+__global__ void __launch_bounds__(kThreads) k_plain_grid_g(const uint8_t* __restrict__ volt, int t0, int C, int A,
+                                                           int P, int N, const int4* __restrict__ box,
+                                                           const int* __restrict__ cell_off,
+                                                           const int* __restrict__ cell_ptr,
+                                                           const int* __restrict__ ce, const float2* __restrict__ cw,
+                                                           float2* __restrict__ grid)
+{
+    const int tl = blockIdx.x, c = blockIdx.y;
+    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
+    const int4 b = box[c];
+    const int* ptr = cell_ptr + cell_off[c];
+    const size_t NN = (size_t)N * N;
+    float2* g = grid + ((size_t)tl * C + c) * P * NN;
+    for (int cell = threadIdx.x; cell < N * N; cell += blockDim.x) {
+        const int y = cell / N, x = cell - y * N;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        const int rx = x - b.x, ry = y - b.y;
+        if (rx >= 0 && rx < b.z && ry >= 0 && ry < b.w) {
+            const int r = ry * b.z + rx;
+            const int q1 = ptr[r + 1];
+            for (int q = ptr[r]; q < q1; ++q) {
+                const int e = ce[q];
+                const float2 w = cw[q];
+                a0 = cfma(w, unpack44(__ldg(fr + (size_t)e * P)), a0);
+                if (P == 2) a1 = cfma(w, unpack44(__ldg(fr + (size_t)e * P + 1)), a1);
+            }
+        }
+        g[cell] = a0;
+        if (P == 2) g[NN + cell] = a1;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_plain_fft_rows(float2* __restrict__ grid, size_t n_rows, int logN,
                                                              int rows_per_cta, const float2* __restrict__ twg)
 {
@@ -167,11 +202,7 @@ epic_status plain_setup(epic_plan_s* p)
     if (st != EPIC_OK) return st;
     cudaError_t e = cudaSuccess;
     const size_t sg = sizeof(float2) * (size_t)p->A * p->P;
-    if (sg > 48 * 1024) {
-        if ((int)sg > p->smem_optin) {
-            p->last_error = "plain path: frame of A*P voltages does not fit in shared memory";
-            return EPIC_ERR_UNSUPPORTED;
-        }
+    if (sg > 48 * 1024 && (int)sg <= p->smem_optin) {  // larger frames use k_plain_grid_g
         e = allow_max_smem((const void*)k_plain_grid, p->smem_optin);
         if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_plain_grid)");
     }
@@ -190,8 +221,12 @@ epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     for (int t0 = 0; t0 < T; t0 += p->time_chunk) {
         const int nt = std::min(p->time_chunk, T - t0);
         ev_begin(p, "k_plain_grid", s);
-        k_plain_grid<<<dim3(nt, C), kThreads, sg, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off,
-                                                       p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
+        if ((int)sg <= p->smem_optin)
+            k_plain_grid<<<dim3(nt, C), kThreads, sg, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off,
+                                                           p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
+        else
+            k_plain_grid_g<<<dim3(nt, C), kThreads, 0, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off,
+                                                            p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
         ev_end(p, s);
         const size_t n_rows = (size_t)nt * C * P * N;
         const int rpc = rows_per_cta_for(N);

@@ -60,6 +60,16 @@ def test_fft2_matches_naive_dft_and_numpy(n):
     assert np.abs(got - np.fft.ifft2(g) * n * n).max() <= 1e-12 * max(1.0, np.abs(naive).max())
 
 
+@pytest.mark.parametrize("n", [256, 512])
+def test_fft2_large_grids_match_numpy(n):
+    # the largest grids the library takes (512 x 512): against numpy's inverse FFT x N^2
+    rng = np.random.default_rng(n + 1)
+    g = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    got = oracle.fft2(g)
+    ref = np.fft.ifft2(g) * n * n
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
 def test_fft2_single_impulse_is_plane_wave():
     n = 16
     g = np.zeros((n, n), complex)

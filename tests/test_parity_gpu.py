@@ -177,3 +177,23 @@ def test_one_plan_many_block_lengths(path):
         for T in (1, 8, 3, 40, 13, 2, 29):
             got = plan.image(d[:T].contiguous()).cpu().numpy()
             assert_parity(got, oracle_image(cfg, v[:T]), path, f"T={T}")
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+def test_512_grid_matches_oracle(path):
+    # the largest grid the library takes, a sparse array whose occupied box is 90 cells wide
+    cfg = synth.small_config(n_ant=60, n_chan=2, n_pol=2, grid_n=512, gcf_k=3, n_time=3, seed=31,
+                             diameter_m=0.32 * 90 * 2.0, sigma=0.7)
+    v = synth.make_voltages(cfg)
+    got = run_gpu(cfg, v, path)
+    assert_parity(got, oracle_image(cfg, v), path, "512 grid")
+
+
+def test_large_grid_workload_plain_sampled():
+    # 20,000 dual-pol elements on a 512 x 512 grid: one frame of voltages (40 KB of bytes,
+    # 320 KB unpacked) exceeds shared memory, so the plain path grids from global memory
+    cfg = synth.config(6)
+    cfg.n_time = 2
+    v = synth.make_voltages(cfg)
+    got = run_gpu(cfg, v, "plain")
+    assert_parity(got, oracle_image(cfg, v), "plain", cfg.name)
