@@ -52,6 +52,8 @@ class EpicConfig:
     src_amp: np.ndarray        # float64 [S], rms amplitude of each source
     noise_sigma: float
     seed: int
+    input_bits: int = 4        # 4: 4+4-bit bytes; 8: 8+8-bit (real byte, imaginary byte)
+    sub_int: int = 0           # time samples per output image (0 = the whole block)
 
     @property
     def n_ant(self) -> int:
@@ -71,7 +73,7 @@ class EpicConfig:
 
     def voltage_bytes(self, n_time: Optional[int] = None) -> int:
         t = self.n_time if n_time is None else n_time
-        return t * self.n_chan * self.n_ant * self.n_pol
+        return t * self.n_chan * self.n_ant * self.n_pol * (2 if self.input_bits == 8 else 1)
 
     def image_floats(self) -> int:
         return self.n_chan * self.n_prod * self.grid_n * self.grid_n
@@ -194,7 +196,9 @@ def source_phases(cfg: EpicConfig) -> np.ndarray:
 
 def make_voltages(cfg: EpicConfig, t0: int = 0, n_time: Optional[int] = None,
                   out: Optional[np.ndarray] = None) -> np.ndarray:
-    """uint8[T][C][A][P] packed 4+4-bit voltages for time samples [t0, t0+T).
+    """uint8[T][C][A][P] packed 4+4-bit voltages for time samples [t0, t0+T), or
+    uint8[T][C][A][P][2] 8+8-bit ones (two's complement real, imaginary bytes) when
+    cfg.input_bits == 8.
 
     Noise and source amplitudes are drawn in float32 from the stream of each
     time sample; the source term is a batched (A x S) @ (S x P) product per
@@ -203,8 +207,9 @@ def make_voltages(cfg: EpicConfig, t0: int = 0, n_time: Optional[int] = None,
     T = cfg.n_time - t0 if n_time is None else int(n_time)
     C, A, P = cfg.n_chan, cfg.n_ant, cfg.n_pol
     S = cfg.src_lm.shape[0]
+    eight = getattr(cfg, "input_bits", 4) == 8
     if out is None:
-        out = np.empty((T, C, A, P), dtype=np.uint8)
+        out = np.empty((T, C, A, P, 2) if eight else (T, C, A, P), dtype=np.uint8)
     ph = source_phases(cfg).astype(np.complex64) if S else None       # [C][A][S]
     amp = (cfg.src_amp / math.sqrt(2.0)).astype(np.float32)
     for i in range(T):
@@ -219,7 +224,11 @@ def make_voltages(cfg: EpicConfig, t0: int = 0, n_time: Optional[int] = None,
             src = np.matmul(ph, a.astype(np.complex64))                    # [C][A][P]
             re = re + src.real
             im = im + src.imag
-        out[i] = pack_nibbles(np.clip(np.rint(re), -7, 7), np.clip(np.rint(im), -7, 7))
+        if eight:  # 8+8-bit: the same signal on a 16x finer scale, clipped to +-127
+            q = np.stack([np.clip(np.rint(16.0 * re), -127, 127), np.clip(np.rint(16.0 * im), -127, 127)], axis=-1)
+            out[i] = q.astype(np.int8).view(np.uint8)
+        else:
+            out[i] = pack_nibbles(np.clip(np.rint(re), -7, 7), np.clip(np.rint(im), -7, 7))
     return out
 
 

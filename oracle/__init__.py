@@ -13,6 +13,6 @@ inverse FFT, Parseval, closed-form one- and two-element images, point-source
 localisation, time linearity, and the pairwise-correlation brute force).
 """
 from .oracle import (  # noqa: F401
-    GCF_GAUSSIAN, GCF_TABLE, build, lib, unpack_table, fft2, footprint, grid_frame, image, image_cfg, max_threads,
+    GCF_GAUSSIAN, GCF_TABLE, build, lib, unpack_table, unpack8_pairs, fft2, footprint, grid_frame, image, image_cfg, max_threads,
     OracleError,
 )

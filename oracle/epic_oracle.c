@@ -25,12 +25,14 @@
  *   - Gaussian GCF W(d) = exp(-|d|^2 / (2 sigma_c^2)) in cells, not renormalised;
  *     sigma_c = sigma * f_c / f_ref when frequency scaled.  Tabulated GCF: complex
  *     samples at offsets (i/os - K/2) per axis, nearest sample (ties up).
- *   - Unpack: real part = high nibble, imaginary = low nibble, two's complement.
+ *   - Unpack: real part = high nibble, imaginary = low nibble, two's complement; for
+ *     8+8-bit input (paper Sec. 4) the real byte precedes the imaginary byte.
  *   - d2r_j = 1, transform sign +, no 1/N; the image index i stores Fourier index
  *     k = (i + N/2) mod N (fftshift), rows = y (m), columns = x (l).
  *   - Products: XX = |E_X|^2, YY = |E_Y|^2, XY = E_X conj(E_Y) stored as Re, Im;
  *     YX = conj(XY) is not stored.  One pol: XX only.
- *   - <.> is the SUM over the block's time samples (the caller divides by T).
+ *   - <.> is the SUM over the block's time samples (the caller divides by T), or over
+ *     each interval of `sub` samples when sub-integrations are asked for (Sec. 4).
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,6 +57,15 @@ void eo_unpack(uint8_t b, int* re, int* im)
 {
     *re = eo_nibble((unsigned)b >> 4);
     *im = eo_nibble((unsigned)b & 0xFu);
+}
+
+/* ---- unpack (8+8-bit two's complement: real byte, then imaginary byte) ---------- */
+static int eo_byte(unsigned v) { return (v & 0x80u) ? (int)v - 256 : (int)v; }
+
+void eo_unpack8(const uint8_t* b, int* re, int* im)
+{
+    *re = eo_byte(b[0]);
+    *im = eo_byte(b[1]);
 }
 
 /* ---- geometry and GCF footprint of one channel (Eq. 1 bracket: W(r_j - r_e)) ---- */
@@ -171,12 +182,13 @@ int eo_fft2(double* g, int N)
 
 /* ---- gridding of one (t, c, p) frame: G[j] = sum_e w_e(j) E_e^p (Eq. 1 bracket) --- */
 static void eo_grid(int n_ant, int K, int N, const int* tap_x, const int* tap_y, const double* w,
-                    const uint8_t* frame /* [A][P] */, int P, int p, double* g /* [N][N][2] */)
+                    const uint8_t* frame /* [A][P] samples */, int P, int p, int bits, double* g /* [N][N][2] */)
 {
     memset(g, 0, sizeof(double) * 2 * (size_t)N * N);
     for (int e = 0; e < n_ant; ++e) {
         int vr, vi;
-        eo_unpack(frame[e * P + p], &vr, &vi);
+        if (bits == 8) eo_unpack8(frame + 2 * ((size_t)e * P + p), &vr, &vi);
+        else eo_unpack(frame[e * P + p], &vr, &vi);
         for (int ty = 0; ty < K; ++ty) {
             for (int tx = 0; tx < K; ++tx) {
                 const double* c = w + (((size_t)e * K + ty) * K + tx) * 2;
@@ -205,7 +217,7 @@ int eo_grid_frame(int n_ant, const double* pos_m, int n_pol, int n_chan, const d
                           f_ref_hz, freq_scaled, oversample, table, tx, ty, w);
         if (rc == EO_OK) {
             const uint8_t* frame = volt + ((size_t)t * n_chan + c) * (size_t)n_ant * n_pol;
-            eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, g);
+            eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, 4, g);
         }
     }
     free(tx); free(ty); free(w);
@@ -213,18 +225,25 @@ int eo_grid_frame(int n_ant, const double* pos_m, int n_pol, int n_chan, const d
 }
 
 /* ---- whole path for a set of channels ---------------------------------------- */
-/* volt: uint8[T][n_chan][A][P]; chans: n_sel channel indices (NULL = all);
- * out: double[n_sel][nprod][N][N] with nprod = 1 (P = 1) or 4 (XX, YY, Re XY, Im XY). */
-int eo_image(int n_ant, const double* pos_m, int n_pol, int n_chan, const double* freq_hz,
-             const double* cell_m, int N, int gcf_kind, int K, double sigma_cells, double f_ref_hz,
-             int freq_scaled, int oversample, const float* table,
-             const uint8_t* volt, int T, int n_sel, const int* chans, double* out, int n_threads)
+/* volt: uint8[T][n_chan][A][P] (bits = 4: one byte per sample) or uint8[T][n_chan][A][P][2]
+ * (bits = 8: real byte, imaginary byte); chans: n_sel channel indices (NULL = all);
+ * sub: time samples per output image (0 = one image set for the whole block; T a multiple of sub);
+ * out: double[n_int][n_sel][nprod][N][N] with n_int = T / sub (1 when sub = 0) and nprod = 1
+ * (P = 1) or 4 (XX, YY, Re XY, Im XY): Eq. 2's average taken (as a sum) over each interval. */
+int eo_image_ext(int n_ant, const double* pos_m, int n_pol, int n_chan, const double* freq_hz,
+                 const double* cell_m, int N, int gcf_kind, int K, double sigma_cells, double f_ref_hz,
+                 int freq_scaled, int oversample, const float* table,
+                 const uint8_t* volt, int T, int bits, int sub, int n_sel, const int* chans, double* out,
+                 int n_threads)
 {
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_chan < 1 || N < 2 || (N & (N - 1)) || K < 1 ||
-        T < 0 || n_sel < 0)
+        T < 0 || n_sel < 0 || (bits != 4 && bits != 8) || sub < 0 || (sub > 0 && T % sub != 0))
         return EO_ERR_ARG;
     if (!chans) n_sel = n_chan;
     int nprod = n_pol == 1 ? 1 : 4;
+    const int n_int = sub > 0 ? T / sub : 1;
+    const int span = sub > 0 ? sub : T;            /* samples per interval */
+    const size_t bytes = bits == 8 ? 2 : 1;        /* per complex sample */
     int status = EO_OK;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -247,36 +266,49 @@ int eo_image(int n_ant, const double* pos_m, int n_pol, int n_chan, const double
                 status = rc;
             } else {
                 size_t NN = (size_t)N * N;
-                for (int t = 0; t < T; ++t) {
-                    const uint8_t* frame = volt + ((size_t)t * n_chan + c) * (size_t)n_ant * n_pol;
-                    for (int p = 0; p < n_pol; ++p) {
-                        eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, g + p * 2 * NN);
-                        eo_fft2(g + p * 2 * NN, N);
-                    }
-                    for (size_t k = 0; k < NN; ++k) {
-                        double xr = g[2 * k], xi = g[2 * k + 1];
-                        acc[k] += xr * xr + xi * xi;
-                        if (n_pol == 2) {
-                            double yr = g[2 * NN + 2 * k], yi = g[2 * NN + 2 * k + 1];
-                            acc[NN + k] += yr * yr + yi * yi;
-                            acc[2 * NN + k] += xr * yr + xi * yi;   /* Re X conj(Y) */
-                            acc[3 * NN + k] += xi * yr - xr * yi;   /* Im X conj(Y) */
+                for (int iv = 0; iv < n_int; ++iv) {
+                    memset(acc, 0, sizeof(double) * (size_t)nprod * NN);
+                    for (int t = iv * span; t < (iv + 1) * span; ++t) {
+                        const uint8_t* frame = volt + ((size_t)t * n_chan + c) * (size_t)n_ant * n_pol * bytes;
+                        for (int p = 0; p < n_pol; ++p) {
+                            eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, bits, g + p * 2 * NN);
+                            eo_fft2(g + p * 2 * NN, N);
+                        }
+                        for (size_t k = 0; k < NN; ++k) {
+                            double xr = g[2 * k], xi = g[2 * k + 1];
+                            acc[k] += xr * xr + xi * xi;
+                            if (n_pol == 2) {
+                                double yr = g[2 * NN + 2 * k], yi = g[2 * NN + 2 * k + 1];
+                                acc[NN + k] += yr * yr + yi * yi;
+                                acc[2 * NN + k] += xr * yr + xi * yi;   /* Re X conj(Y) */
+                                acc[3 * NN + k] += xi * yr - xr * yi;   /* Im X conj(Y) */
+                            }
                         }
                     }
+                    /* fftshift on output: image index i holds Fourier index (i + N/2) mod N */
+                    double* o = out + ((size_t)iv * n_sel + s) * nprod * NN;
+                    for (int q = 0; q < nprod; ++q)
+                        for (int iy = 0; iy < N; ++iy)
+                            for (int ix = 0; ix < N; ++ix) {
+                                int ky = (iy + N / 2) % N, kx = (ix + N / 2) % N;
+                                o[q * NN + (size_t)iy * N + ix] = acc[q * NN + (size_t)ky * N + kx];
+                            }
                 }
-                /* fftshift on output: image index i holds Fourier index (i + N/2) mod N */
-                double* o = out + (size_t)s * nprod * NN;
-                for (int q = 0; q < nprod; ++q)
-                    for (int iy = 0; iy < N; ++iy)
-                        for (int ix = 0; ix < N; ++ix) {
-                            int ky = (iy + N / 2) % N, kx = (ix + N / 2) % N;
-                            o[q * NN + (size_t)iy * N + ix] = acc[q * NN + (size_t)ky * N + kx];
-                        }
             }
         }
         free(tx); free(ty); free(w); free(g); free(acc);
     }
     return status;
+}
+
+/* The 4+4-bit, whole-block form of eo_image_ext. */
+int eo_image(int n_ant, const double* pos_m, int n_pol, int n_chan, const double* freq_hz,
+             const double* cell_m, int N, int gcf_kind, int K, double sigma_cells, double f_ref_hz,
+             int freq_scaled, int oversample, const float* table,
+             const uint8_t* volt, int T, int n_sel, const int* chans, double* out, int n_threads)
+{
+    return eo_image_ext(n_ant, pos_m, n_pol, n_chan, freq_hz, cell_m, N, gcf_kind, K, sigma_cells, f_ref_hz,
+                        freq_scaled, oversample, table, volt, T, 4, 0, n_sel, chans, out, n_threads);
 }
 
 int eo_max_threads(void)

@@ -56,6 +56,10 @@ def lib():
             L.eo_grid_frame.restype = i
             L.eo_image.argtypes = plan + [P(ctypes.c_uint8), i, i, P(i), P(d), i]
             L.eo_image.restype = i
+            L.eo_image_ext.argtypes = plan + [P(ctypes.c_uint8), i, i, i, i, P(i), P(d), i]
+            L.eo_image_ext.restype = i
+            L.eo_unpack8.argtypes = [P(ctypes.c_uint8), P(i), P(i)]
+            L.eo_unpack8.restype = None
             L.eo_max_threads.argtypes = []
             L.eo_max_threads.restype = i
             _lib = L
@@ -84,6 +88,18 @@ def unpack_table() -> np.ndarray:
     for v in range(256):
         L.eo_unpack(v, ctypes.byref(a), ctypes.byref(b))
         out[v] = (a.value, b.value)
+    return out
+
+
+def unpack8_pairs(pairs: np.ndarray) -> np.ndarray:
+    """int[n][2]: the oracle's (re, im) for 8+8-bit byte pairs uint8[n][2]."""
+    L = lib()
+    pr = np.ascontiguousarray(pairs, dtype=np.uint8).reshape(-1, 2)
+    out = np.zeros((pr.shape[0], 2), dtype=np.int64)
+    a, b = ctypes.c_int(), ctypes.c_int()
+    for k in range(pr.shape[0]):
+        L.eo_unpack8(_p(pr[k], ctypes.c_uint8), ctypes.byref(a), ctypes.byref(b))
+        out[k] = (a.value, b.value)
     return out
 
 
@@ -146,29 +162,35 @@ def grid_frame(volt: np.ndarray, t: int, c: int, p: int, pos_m, freq_hz, n_pol: 
 
 def image(volt: np.ndarray, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int, sigma_cells: float,
           f_ref_hz: float = 1.0, freq_scaled: bool = False, cell_m=None, chans: Optional[Sequence[int]] = None,
-          gcf_kind: int = GCF_GAUSSIAN, oversample: int = 1, table=None, threads: int = 0) -> np.ndarray:
-    """float64[n_sel][nprod][N][N]: accumulated images of the selected channels.
+          gcf_kind: int = GCF_GAUSSIAN, oversample: int = 1, table=None, threads: int = 0,
+          input_bits: int = 4, sub_int: int = 0) -> np.ndarray:
+    """Accumulated images of the selected channels: float64[n_sel][nprod][N][N], or with
+    sub-integrations (sub_int > 0) float64[T / sub_int][n_sel][nprod][N][N].
 
-    volt is uint8[T][C][A][P] holding ALL channels; chans selects which are imaged.
+    volt holds ALL channels: uint8[T][C][A][P] (4+4-bit) or uint8[T][C][A][P][2] (8+8-bit:
+    real byte, imaginary byte); chans selects which are imaged.
     """
     geo = _Geom(pos_m, freq_hz, cell_m, n_pol, grid_n, gcf_kind, gcf_k, sigma_cells, f_ref_hz, freq_scaled,
                 oversample, table)
     v = np.ascontiguousarray(volt, dtype=np.uint8)
     T = v.shape[0]
     C = geo.freq.shape[0]
-    if v.size != T * C * geo.pos.shape[0] * geo.n_pol:
-        raise OracleError("voltage array does not match T x C x A x P")
+    per = 2 if input_bits == 8 else 1
+    if v.size != T * C * geo.pos.shape[0] * geo.n_pol * per:
+        raise OracleError("voltage array does not match T x C x A x P (x 2 for 8+8-bit)")
     sel = None if chans is None else np.ascontiguousarray(chans, dtype=np.int32)
     n_sel = C if sel is None else sel.shape[0]
     nprod = 1 if n_pol == 1 else 4
-    out = np.zeros((n_sel, nprod, grid_n, grid_n), dtype=np.float64)
-    rc = lib().eo_image(*geo.args(), _p(v, ctypes.c_uint8), T, n_sel, _p(sel, ctypes.c_int),
-                        _p(out, ctypes.c_double), int(threads))
+    n_int = T // sub_int if sub_int > 0 else 1
+    out = np.zeros((n_int, n_sel, nprod, grid_n, grid_n), dtype=np.float64)
+    rc = lib().eo_image_ext(*geo.args(), _p(v, ctypes.c_uint8), T, int(input_bits), int(sub_int), n_sel,
+                            _p(sel, ctypes.c_int), _p(out, ctypes.c_double), int(threads))
     _check(rc, "image")
-    return out
+    return out if sub_int > 0 else out[0]
 
 
 def image_cfg(cfg, volt: np.ndarray, chans: Optional[Sequence[int]] = None, threads: int = 0) -> np.ndarray:
-    """image() for an ``epic_synth.EpicConfig``."""
+    """image() for an ``epic_synth.EpicConfig`` (its input bits and sub-integration)."""
     return image(volt, cfg.pos_m, cfg.freq_hz, cfg.n_pol, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells,
-                 cfg.f_ref_hz, cfg.freq_scaled, None, chans, threads=threads)
+                 cfg.f_ref_hz, cfg.freq_scaled, None, chans, threads=threads,
+                 input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0))

@@ -4,6 +4,7 @@ None of these compare the oracle with itself: each check uses an independent
 route (hand-written codes, numpy's inverse FFT, a naive DFT matrix, closed
 forms, Parseval, the pairwise-correlation brute force, invariants).
 """
+import dataclasses
 import json
 import math
 import os
@@ -306,3 +307,60 @@ def test_table_gcf_matches_bruteforce(K, os_):
     b = bruteforce.image(v, cfg.pos_m, cfg.freq_hz, 2, 16, K, cfg.sigma_cells, table=tab, oversample=os_)
     assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
     assert np.abs(a[:, 3]).max() > 1e-3 * np.abs(a).max()                  # XY carries a real phase
+
+
+# ----------------------------------------------------------------------------- 8+8-bit input, sub-integrations
+
+def test_unpack8_matches_twos_complement_bytes():
+    # every value of the real and of the imaginary byte, against numpy's int8 view
+    v = np.arange(256, dtype=np.uint8)
+    pairs = np.stack([v, v[::-1]], axis=1)
+    got = oracle.unpack8_pairs(pairs)
+    assert np.array_equal(got[:, 0], v.view(np.int8).astype(np.int64))
+    assert np.array_equal(got[:, 1], v[::-1].view(np.int8).astype(np.int64))
+
+
+def test_eight_bit_block_images_equal_four_bit_block_with_same_values():
+    # the same complex samples written in both formats give identical images
+    cfg = synth.small_config(n_ant=12, n_chan=2, n_pol=2, grid_n=16, gcf_k=3, n_time=5, seed=41)
+    v4 = synth.make_voltages(cfg)
+    E = bruteforce.decode_nibbles(v4)                           # [T][C][A][P] complex, from the pinned table
+    v8 = np.stack([E.real, E.imag], axis=-1).astype(np.int8).view(np.uint8)
+    a = oracle.image_cfg(cfg, v4)
+    cfg8 = dataclasses.replace(cfg, input_bits=8)
+    b = oracle.image_cfg(cfg8, v8)
+    assert np.array_equal(a, b)
+
+
+def test_sub_integrations_sum_to_the_block_and_equal_their_sub_blocks():
+    cfg = dataclasses.replace(synth.small_config(n_ant=10, n_chan=2, n_pol=2, grid_n=16, gcf_k=3, n_time=12,
+                                                 seed=42), input_bits=8)
+    v = synth.make_voltages(cfg)
+    whole = oracle.image_cfg(cfg, v)
+    sub = oracle.image_cfg(dataclasses.replace(cfg, sub_int=4), v)
+    assert sub.shape == (3,) + whole.shape
+    assert np.abs(sub.sum(axis=0) - whole).max() <= 1e-12 * np.abs(whole).max()
+    for k in range(3):
+        assert np.array_equal(sub[k], oracle.image_cfg(cfg, v[4 * k:4 * k + 4]))
+
+
+def test_one_frame_transient_found_in_its_sub_integration():
+    # 8+8-bit voltages, 4-frame sub-integrations (paper Sec. 4): a source present in one
+    # frame only peaks at its pixel in that frame's sub-integration and nowhere else
+    N = 32
+    rng = np.random.default_rng(78)
+    pos = synth.layout_disc(48, 14.0, rng)
+    f = np.array([C0 / 2.0])
+    noise = synth.EpicConfig("noise", pos, f, 2, N, 3, 0.5, float(f[0]), False, 12, np.zeros((0, 2)),
+                             np.zeros(0), 2.0, 23, input_bits=8)
+    tran = synth.EpicConfig("transient", pos, f, 2, N, 3, 0.5, float(f[0]), False, 12,
+                            np.array([[-0.5, 0.125]]), np.array([6.0]), 0.0, 24, input_bits=8)
+    vn = synth.make_voltages(noise).view(np.int8).astype(np.int32)
+    vt = synth.make_voltages(tran).view(np.int8).astype(np.int32)
+    x = vn.copy()
+    x[6] += vt[6]                                                # one frame (frame 6, interval 1)
+    v = np.clip(x, -127, 127).astype(np.int8).view(np.uint8)
+    sub = oracle.image_cfg(dataclasses.replace(noise, sub_int=4), v)[:, 0, 0]   # [3][N][N] XX
+    t_pix = (N // 2 + 2, N // 2 - 8)                             # (iy, ix) of (l, m) = (-0.5, 0.125)
+    assert np.unravel_index(np.argmax(sub[1]), sub[1].shape) == t_pix
+    assert sub[1][t_pix] > 5 * max(sub[0][t_pix], sub[2][t_pix])
