@@ -101,6 +101,13 @@ typedef struct {
     epic_gcf_desc gcf;
     int path;               /* epic_path                                                          */
     int max_time;           /* largest T of one call (sizes scratch and host staging), >= 1       */
+    int input_bits;         /* 4 (or 0): one 4+4-bit byte per complex sample, real in the high
+                               nibble; 8: two bytes per sample, real then imaginary, two's
+                               complement (paper Sec. 4)                                          */
+    int sub_int;            /* 0: one image set per call (Eq. 2's average over the whole block);
+                               S > 0: one image set per S samples (sub-integrations, Sec. 4) --
+                               T of every call a multiple of S, 1 <= S <= max_time; the tensor
+                               path needs its control-warp kernel for it (UNSUPPORTED otherwise) */
 } epic_plan_desc;
 
 typedef struct epic_plan_s* epic_plan_t;
@@ -118,6 +125,8 @@ typedef struct {
     double gemm_flops_per_sample; /* DFT-as-GEMM path: flops of the pruned two-stage transform per
                                      time sample over all channels and pols (8 per complex MAC over
                                      the occupied box); 0 for the FFT paths                        */
+    int input_bits;         /* 4 or 8                                                             */
+    int sub_int;            /* samples per image set, 0 = the whole block                         */
 } epic_plan_info;
 
 /* flags of epic_image / epic_image_host */
@@ -138,8 +147,9 @@ epic_status epic_plan_create(const epic_plan_desc* desc, epic_plan_t* out);
 epic_status epic_plan_destroy(epic_plan_t plan);
 
 /* Image one voltage block (Eq. 1-2) on `stream` (a cudaStream_t; NULL = legacy
- * default stream).  volt: device uint8[T][C][A][P]; out: device float32
- * [C][n_prod][N][N], written (EPIC_RESET) or added to (EPIC_ACCUMULATE).
+ * default stream).  volt: device uint8[T][C][A][P] (uint8[T][C][A][P][2] for 8+8-bit
+ * input); out: device float32 [C][n_prod][N][N] ([T/S][C][n_prod][N][N] with
+ * sub-integrations of S samples), written (EPIC_RESET) or added to (EPIC_ACCUMULATE).
  * 0 <= T <= max_time; T = 0 with EPIC_RESET zeroes out.  Asynchronous: returns
  * after launching.  The plan's scratch is reused by every call, so calls on one
  * plan must not overlap on different streams.

@@ -205,6 +205,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
         return bad("unknown gcf.kind");
     }
     if (d->path < EPIC_PATH_PLAIN_FP32 || d->path > EPIC_PATH_AUTO) return bad("unknown path");
+    if (d->input_bits != 0 && d->input_bits != 4 && d->input_bits != 8) return bad("input_bits must be 4 or 8");
+    if (d->sub_int < 0 || d->sub_int > d->max_time) return bad("sub_int must be in 0..max_time");
     if ((long long)d->n_ant * d->n_pol > (1 << 20)) return bad("n_ant * n_pol too large");
     for (int c = 0; c < d->n_chan; ++c) {
         if (!(d->freq_hz[c] > 0.0) || !std::isfinite(d->freq_hz[c])) return bad("freq_hz must be > 0 and finite");
@@ -225,6 +227,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     p->K = d->gcf.K;
     p->nprod = d->n_pol == 1 ? 1 : 4;
     p->max_time = d->max_time;
+    p->bits = d->input_bits == 8 ? 8 : 4;
+    p->sub = d->sub_int;
     p->logN = 0;
     while ((1 << p->logN) < p->N) ++p->logN;
     p->pos.assign(d->pos_m, d->pos_m + 2 * (size_t)d->n_ant);
@@ -337,6 +341,8 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
     else nk = p->scratch ? 2 : 1;
     info->n_kernels = nk;
     info->gemm_flops_per_sample = p->path == EPIC_PATH_DFTGEMM_FP16 ? p->tc_flops_per_sample : 0.0;
+    info->input_bits = p->bits;
+    info->sub_int = p->sub;
     return EPIC_OK;
 }
 
@@ -350,7 +356,7 @@ epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     p->n_events = 0;
     p->last_stream = s;
     if (T == 0) {
-        if (!acc) {
+        if (!acc && p->sub == 0) {  // an empty block: zero images (with sub-integrations: no image set)
             cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)p->C * p->nprod * p->N * p->N, s);
             if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemsetAsync(out)");
         }
@@ -455,6 +461,10 @@ epic_status epic_image(epic_plan_t p, const uint8_t* volt, int T, void* stream, 
         p->last_error = "NULL voltage or image pointer";
         return EPIC_ERR_INVALID_ARG;
     }
+    if (p->sub > 0 && T % p->sub != 0) {
+        p->last_error = "T must be a multiple of the plan's sub_int";
+        return EPIC_ERR_INVALID_ARG;
+    }
     if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS | EPIC_GRAPH)) {
         p->last_error = "unknown flag bits";
         return EPIC_ERR_INVALID_ARG;
@@ -476,8 +486,8 @@ epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void
                             unsigned flags)
 {
     if (!p) return EPIC_ERR_INVALID_ARG;
-    if (T < 0 || T > p->max_time || !out_host || (T > 0 && !volt_host)) {
-        p->last_error = "bad T or NULL host pointer";
+    if (T < 0 || T > p->max_time || !out_host || (T > 0 && !volt_host) || (p->sub > 0 && T % p->sub != 0)) {
+        p->last_error = "bad T (0..max_time, a multiple of sub_int) or NULL host pointer";
         return EPIC_ERR_INVALID_ARG;
     }
     if (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS | EPIC_GRAPH)) {
@@ -485,19 +495,22 @@ epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void
         return EPIC_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t vb = (size_t)p->max_time * p->C * p->A * p->P;
-    const size_t ob = sizeof(float) * (size_t)p->C * p->nprod * p->N * p->N;
+    const size_t vb = (size_t)p->max_time * p->C * p->A * p->P * (p->bits / 4);
+    const size_t sets_max = p->sub > 0 ? (size_t)(p->max_time / p->sub) : 1;
+    const size_t set_bytes = sizeof(float) * (size_t)p->C * p->nprod * p->N * p->N;
+    const size_t ob_max = std::max<size_t>(1, sets_max) * set_bytes;
+    const size_t ob = (p->sub > 0 ? (size_t)(T / p->sub) : 1) * set_bytes;  // this call's image sets
     if (!p->stage_volt) {
         cudaError_t e = cudaMalloc(&p->stage_volt, vb);
-        if (e == cudaSuccess) e = cudaMalloc(&p->stage_out, ob);
+        if (e == cudaSuccess) e = cudaMalloc(&p->stage_out, ob_max);
         if (e != cudaSuccess) {
             cudaFree(p->stage_volt);
             p->stage_volt = nullptr;
             return epic::cuda_fail(p, e, "cudaMalloc(host-call staging)");
         }
-        p->stage_bytes = vb + ob;
+        p->stage_bytes = vb + ob_max;
     }
-    const size_t tb = (size_t)T * p->C * p->A * p->P;
+    const size_t tb = (size_t)T * p->C * p->A * p->P * (p->bits / 4);
     cudaError_t e = cudaSuccess;
     if (tb) e = cudaMemcpyAsync(p->stage_volt, volt_host, tb, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && (flags & EPIC_ACCUMULATE))

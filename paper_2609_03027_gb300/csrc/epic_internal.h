@@ -85,6 +85,8 @@ struct KernelEvent {
 struct epic_plan_s {
     // descriptor copy
     int A = 0, P = 0, C = 0, N = 0, K = 0, nprod = 0, path = 0, max_time = 0;
+    int bits = 4;                         // input samples: 4 (4+4-bit bytes) or 8 (8+8-bit pairs)
+    int sub = 0;                          // samples per image set (0 = the whole block)
     int logN = 0;
     int device = 0;
     std::vector<double> pos, freq, cell;

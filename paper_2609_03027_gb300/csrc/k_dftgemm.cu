@@ -113,6 +113,9 @@ struct MmaArgs {
     const long long* a1p_off;
     float* partial;             // k_dftgemm_ws3: 2 slots per block of 4 x 128 x 64 partial sums
     int* counters;              // k_dftgemm_ws3: per item, blocks that stored a part (reset by the last)
+    int sub;                    // k_dftgemm_ws3<2>: samples per image set
+    int iv0;                    // k_dftgemm_ws3<2>: image set of the chunk's first sample
+    int C;                      // channels of the plan (image sets are [C][nprod][N][N])
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -179,7 +182,7 @@ __device__ __forceinline__ void store_pixels16(float* op, int nk, int accumulate
 template <bool CSR_SMEM, int F>
 __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __restrict__ volt, int t0, int c0,
                                                            int n_ch, int nt, int fpc, int C, int A, int P,
-                                                           const int4* __restrict__ box,
+                                                           int bits, const int4* __restrict__ box,
                                                            const int* __restrict__ cell_off,
                                                            const int* __restrict__ cell_ptr,
                                                            const int* __restrict__ ce,
@@ -212,9 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
         __syncthreads();
         for (int i = threadIdx.x; i < nf * A; i += blockDim.x) {
             const int f = i / A, e = i - f * A;
-            const uint8_t* fr = volt + ((size_t)(t0 + tb + f) * C + c) * (size_t)A * P + (size_t)e * P;
-            const float2 x = unpack44(fr[0]);
-            const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+            const uint8_t* fr = volt + ((size_t)(t0 + tb + f) * C + c) * (size_t)A * P * (bits / 4);
+            const float2 x = load_sample(fr, (size_t)e * P, bits);
+            const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, bits) : make_float2(0.f, 0.f);
             sv[f * A + e] = make_float4(x.x, x.y, y.x, y.y);
         }
         __syncthreads();
@@ -295,12 +298,13 @@ struct GridArgs {
     int* status;
     int max_cells;  // largest nx * ny over the channels
     int max_list;   // largest number of (cell, element) entries of a channel
-    int bulk;       // 1: voltage frames copied by the TMA engine (A*P % 16 == 0, 16-byte aligned base)
+    int bulk;       // 1: voltage frames copied by the TMA engine (frame bytes % 16 == 0, 16-byte aligned base)
+    int bits;       // 4: 4+4-bit bytes, 8: 8+8-bit sample pairs
 };
 
-__host__ __device__ inline size_t grid_ps_smem(int F, int A, int P, int max_cells, int max_list, bool cplx)
+__host__ __device__ inline size_t grid_ps_smem(int F, int A, int frame_bytes, int max_cells, int max_list, bool cplx)
 {
-    const size_t ap = (size_t)((A * P + 15) & ~15);
+    const size_t ap = (size_t)((frame_bytes + 15) & ~15);
     size_t b = 2ull * F * ap + 16ull * F * A + 4ull * ((max_cells + 2) & ~1);
     b += cplx ? 4ull * ((max_list + 1) & ~1) + 8ull * max_list : 8ull * max_list;
     return b;
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
     extern __shared__ __align__(16) uint8_t gsm[];
     __shared__ uint64_t bar_raw[2];
     const int tid = threadIdx.x;
-    const int A = a.A, P = a.P, AP = A * P;
+    const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
     const int APr = (AP + 15) & ~15;
     uint8_t* raw = gsm;                                                  // [2][F][APr]
     float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);           // [F][A]
@@ -389,17 +393,17 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
             }
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
-                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr + (size_t)e * P;
-                const float2 x = unpack44(fr[0]);
-                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
+                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
+                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
                 sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
             }
         } else {
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
-                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP + (size_t)e * P;
-                const float2 x = unpack44(fr[0]);
-                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
+                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
+                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
                 sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
             }
         }
@@ -495,9 +499,10 @@ struct GridBalArgs {
     unsigned tile_max;      // shared-memory bytes per tile (largest channel)
 };
 
-__host__ __device__ inline size_t grid_bal_smem(int F, int A, int P, int max_tasks, int max_list, unsigned tile_max)
+__host__ __device__ inline size_t grid_bal_smem(int F, int A, int frame_bytes, int max_tasks, int max_list,
+                                               unsigned tile_max)
 {
-    const size_t ap = (size_t)((A * P + 15) & ~15);
+    const size_t ap = (size_t)((frame_bytes + 15) & ~15);
     size_t b = 2ull * F * ap + 16ull * F * A;  // raw voltages, unpacked voltages
     b = (b + 127) & ~(size_t)127;
     b += 2ull * F * tile_max;                  // tile buffers
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
     extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ uint64_t bar_raw[2];
     const int tid = threadIdx.x;
-    const int A = a.A, P = a.P, AP = A * P;
+    const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
     const int APr = (AP + 15) & ~15;
     uint8_t* raw = gsm;                                                // [2][F][APr]
     float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);         // [F][A]
@@ -590,17 +595,17 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
             }
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
-                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr + (size_t)e * P;
-                const float2 x = unpack44(fr[0]);
-                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
+                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
+                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
                 sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
             }
         } else {
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
-                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP + (size_t)e * P;
-                const float2 x = unpack44(fr[0]);
-                const float2 y = P == 2 ? unpack44(fr[1]) : make_float2(0.f, 0.f);
+                const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
+                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
+                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
                 sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
             }
         }
@@ -1838,7 +1843,7 @@ __device__ __noinline__ void ws3_split_finish(const MmaArgs& a, int item, int c,
     }
 }
 
-template <int SPLIT>
+template <int MODE>  // 0: whole items, 1: equal shares (split items), 2: whole items, sub-integrations
 __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -1888,7 +1893,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         long long w = wb0;
         for (int it = 0;; ++it) {
             int item, fs, nt;  // work item, its first frame and the frames of this segment
-            if (SPLIT) {
+            if (MODE == 1) {
                 if (w >= wb1) break;
                 item = (int)(w / a.nt);
                 fs = (int)(w % a.nt);
@@ -1978,7 +1983,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         long long w = wb0;
         for (int it = 0;; ++it) {
             int item, fs, nt;  // work item, its first frame and the frames of this segment
-            if (SPLIT) {
+            if (MODE == 1) {
                 if (w >= wb1) break;
                 item = (int)(w / a.nt);
                 fs = (int)(w % a.nt);
@@ -2028,6 +2033,25 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 yc1 = (nyc * (j4 + 1)) >> 2;
             }
             const uint32_t e2addr = tmem + lane_base + 256 + 64 * P * h2 + 16 * (j4 & 1);
+            // sub-integrations: after frame f (chunk-local) ends an interval, write (or add)
+            // the sums to image set iv0 + f / sub and restart them
+            auto flush_interval = [&](int f) {
+                const int ky = 128 * kb + 32 * q4 + lane;
+                const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
+                if (ky < a.N && kx0 < a.N) {
+                    const size_t NN = (size_t)a.N * a.N;
+                    float* o = a.out + ((size_t)(a.iv0 + f / a.sub) * a.C + c) * a.nprod * NN + (size_t)ky * a.N + kx0;
+                    const int nk = min(16, a.N - kx0);
+                    store_pixels16(o, nk, a.accumulate, axx);
+                    if (a.nprod == 4) {
+                        store_pixels16(o + NN, nk, a.accumulate, ayy);
+                        store_pixels16(o + 2 * NN, nk, a.accumulate, arx);
+                        store_pixels16(o + 3 * NN, nk, a.accumulate, aix);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+            };
             bool live = true;
             for (int t = 0; t < nt && live; ++t) {
                 const int sl = t & 1;
@@ -2052,6 +2076,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&d2_empty);
+                    if (MODE == 2 && w2 && t % a.sub == 0) flush_interval(t - 1);  // frame t-1 ends one
                 }
                 if (!w || !w2) err_sh = 1;
                 live = !__any_sync(0xffffffffu, err_sh != 0);
@@ -2063,6 +2088,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 __syncwarp();
                 tc::fence_after_sync();
                 if (w2) ws_epilogue2(e2addr, P, axx, ayy, arx, aix);
+                if (MODE == 2 && w2) flush_interval(nt - 1);
             }
             tc::fence_before_sync();
             bar_all(2);
@@ -2072,7 +2098,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             // segment that is only part of its item goes to this block's partial slot
             const int ky = 128 * kb + 32 * q4 + lane;
             const int kx0 = 64 * g + 32 * h2 + 16 * (j4 & 1);
-            if (SPLIT && (fs != 0 || nt != a.nt)) {
+            if (MODE == 1 && (fs != 0 || nt != a.nt)) {
                 const size_t px = (size_t)(32 * q4 + lane) * 64 + 32 * h2 + 16 * (j4 & 1);
                 float* o = a.partial + (2 * (size_t)blockIdx.x + (first_seg ? 0 : 1)) * 4 * 8192 + px;
                 store_pixels16(o, 16, 0, axx);
@@ -2082,7 +2108,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                     store_pixels16(o + 3 * 8192, 16, 0, aix);
                 }
                 ws3_split_finish(a, item, c, ky, kx0, px, U, tid, split_slot, &split_n);
-            } else if (ky < a.N && kx0 < a.N) {
+            } else if (MODE != 2 && ky < a.N && kx0 < a.N) {
                 const size_t NN = (size_t)a.N * a.N;
                 float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * a.N + kx0;
                 const int nk = min(16, a.N - kx0);
@@ -2108,7 +2134,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 // chunk) take at most `budget` bytes, and the tile buffer for them.
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 {
-    if (!p->tc.ws || variant < 1 || variant > 3) return EPIC_ERR_UNSUPPORTED;
+    if (!p->tc.ws || variant < 1 || variant > 3 || (p->sub > 0 && variant != 3)) return EPIC_ERR_UNSUPPORTED;
     p->tc.ws_variant = variant;
     return EPIC_OK;
 }
@@ -2117,7 +2143,7 @@ epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 // items than SMs), 0 = whole items per block, 1 = equal (item, frame) shares.
 epic_status dftgemm_set_split(epic_plan_s* p, int mode)
 {
-    if (!p->tc.ws || mode < -1 || mode > 1) return EPIC_ERR_UNSUPPORTED;
+    if (!p->tc.ws || mode < -1 || mode > 1 || (p->sub > 0 && mode == 1)) return EPIC_ERR_UNSUPPORTED;
     p->tc.split = mode;
     return EPIC_OK;
 }
@@ -2125,7 +2151,8 @@ epic_status dftgemm_set_split(epic_plan_s* p, int mode)
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
 {
     const size_t per_t = (size_t)p->tc.cg * p->tc.stride;
-    const int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    if (p->sub > 0) tcn = std::max(p->sub, tcn - tcn % p->sub);  // whole sub-integrations per chunk
     const size_t bytes = per_t * tcn;
     p->chunk_budget = budget;
     p->tc.tc = tcn;
@@ -2148,7 +2175,8 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F)
 {
     if (p->tc.grid_variant == 2) return grid_bal_config(p, F);
     if (F != 1 && F != 2 && F != 4 && F != 8) return EPIC_ERR_UNSUPPORTED;
-    const size_t bytes = grid_ps_smem(F, p->A, p->P, p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
+    const size_t bytes =
+        grid_ps_smem(F, p->A, p->A * p->P * (p->bits / 4), p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
     const void* fn = nullptr;
     if (p->tc.grid_cplx) {
         fn = F == 8 ? (const void*)k_dftgemm_grid_ps<true, 8> : F == 4 ? (const void*)k_dftgemm_grid_ps<true, 4>
@@ -2178,7 +2206,8 @@ epic_status dftgemm_grid_config(epic_plan_s* p, int F)
 static epic_status grid_bal_config(epic_plan_s* p, int F)
 {
     if (!p->tc.gtask || (F != 1 && F != 2 && F != 4)) return EPIC_ERR_UNSUPPORTED;
-    const size_t bytes = grid_bal_smem(F, p->A, p->P, p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride);
+    const size_t bytes =
+        grid_bal_smem(F, p->A, p->A * p->P * (p->bits / 4), p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride);
     const void* fn = F == 4 ? (const void*)k_dftgemm_grid_bal<4>
                    : F == 2 ? (const void*)k_dftgemm_grid_bal<2> : (const void*)k_dftgemm_grid_bal<1>;
     cudaFuncAttributes fa{};
@@ -2592,8 +2621,13 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws2<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2>, p->smem_optin);
     p->tc.ws_variant = p->tc.ws ? 3 : 0;
     if (p->tc.ws && p->sm_count > kWs3MaxBlocks) p->tc.ws_variant = 1;
+    if (p->sub > 0 && (!p->tc.ws || p->tc.ws_variant != 3)) {
+        p->last_error = "tensor path: sub-integrations need the control-warp kernel (occupied grid too large)";
+        return EPIC_ERR_UNSUPPORTED;
+    }
     if (p->tc.ws && e == cudaSuccess) {
         const size_t n_items = (size_t)p->tc.cg * n_kb * n_gp;
         e = cudaMalloc(&p->tc.partial, (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float));
@@ -2666,7 +2700,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 g.status = p->tc.status;
                 g.max_cells = p->tc.grid_max_cells;
                 g.max_list = p->tc.grid_max_list;
-                g.bulk = ((A * P) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
+                g.bits = p->bits;
+                g.bulk = ((A * P * (p->bits / 4)) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
                 const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
                 ev_begin(p, "k_dftgemm_grid", s);
                 if (p->tc.grid_variant == 2) {
@@ -2701,7 +2736,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             } else {
             ev_begin(p, "k_dftgemm_grid", s);
 #define EPIC_GRID_LAUNCH(CS, FF)                                                                                    \
-    k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->dt.box,       \
+    k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->bits,         \
+                                                              p->dt.box,                                               \
                                                               p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,         \
                                                               p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride)
             if (p->tc.grid_csr_smem) {
@@ -2719,7 +2755,10 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             a.c0 = c0;
             a.n_ch = ng;
             a.nt = nt;
-            a.accumulate = (accumulate || t0 > 0) ? 1 : 0;
+            a.accumulate = (accumulate || (t0 > 0 && p->sub == 0)) ? 1 : 0;
+            a.sub = p->sub;
+            a.iv0 = p->sub > 0 ? t0 / p->sub : 0;
+            a.C = C;
             const int items = ng * a.n_kb * (p->tc.ws ? p->tc.n_gp : a.n_s);
             const int grid = std::min(items, p->sm_count);
             ev_begin(p, p->tc.ws ? (p->tc.ws_variant == 3 ? "k_dftgemm_ws3" : p->tc.ws_variant == 2 ? "k_dftgemm_ws2" : "k_dftgemm_ws")
@@ -2729,7 +2768,9 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 if (p->tc.ws_variant == 3) {
                     a.partial = p->tc.partial;
                     a.counters = p->tc.counters;
-                    if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
+                    if (p->sub > 0)
+                        k_dftgemm_ws3<2><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                    else if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
                         k_dftgemm_ws3<1><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a);
                     else
                         k_dftgemm_ws3<0><<<grid, kWs3Threads, p->tc.smem, s>>>(a);

@@ -35,6 +35,8 @@ struct FusedArgs {
     float* out;
     int accumulate;
     int box_x, box_y;  // largest occupied box (for shared-memory carving)
+    int bits;          // 4: 4+4-bit bytes, 8: 8+8-bit sample pairs
+    int sub;           // samples per output image set (0 = the whole block)
 };
 
 // Shared memory carve-up (float2 units):
@@ -77,11 +79,32 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fp32(FusedArgs a)
         float axx[NPT], ayy[NPT], arx[NPT], aix[NPT];
 #pragma unroll
         for (int i = 0; i < NPT; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+        // write (or add) this thread's pixels to image set iv, then restart the sums
+        auto store_images = [&](int iv) {
+            const int kx = s * SW + kxl;
+            if (kx < N) {
+                const size_t NN = (size_t)N * N;
+#pragma unroll
+                for (int j = 0; j < NPT; ++j) {
+                    const int ky = ky0 + j * kys;
+                    if (ky >= N) continue;
+                    float* o = a.out + ((size_t)iv * a.C + c) * a.nprod * NN + (size_t)ky * N + kx;
+                    o[0] = (a.accumulate ? o[0] : 0.f) + axx[j];
+                    if (a.nprod == 4) {
+                        o[NN] = (a.accumulate ? o[NN] : 0.f) + ayy[j];
+                        o[2 * NN] = (a.accumulate ? o[2 * NN] : 0.f) + arx[j];
+                        o[3 * NN] = (a.accumulate ? o[3 * NN] : 0.f) + aix[j];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NPT; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
+        };
 
         for (int t = 0; t < a.T; ++t) {
             __syncthreads();
-            const uint8_t* fr = a.volt + ((size_t)t * a.C + c) * (size_t)A * P;
-            for (int i = threadIdx.x; i < A * P; i += blockDim.x) vs[i] = unpack44(fr[i]);
+            const uint8_t* fr = a.volt + ((size_t)t * a.C + c) * (size_t)A * P * (a.bits / 4);
+            for (int i = threadIdx.x; i < A * P; i += blockDim.x) vs[i] = load_sample(fr, i, a.bits);
             __syncthreads();
             // ---- rows: grid 16-row chunks, FFT along x, keep the slab columns
             for (int r0 = 0; r0 < nyp; r0 += kRowChunk) {
@@ -145,24 +168,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fp32(FusedArgs a)
                     }
                 }
             }
+            if (a.sub > 0 && (t + 1) % a.sub == 0) store_images(t / a.sub);  // a sub-integration ends
         }
-        // ---- images
-        const int kx = s * SW + kxl;
-        if (kx < N) {
-            const size_t NN = (size_t)N * N;
-#pragma unroll
-            for (int j = 0; j < NPT; ++j) {
-                const int ky = ky0 + j * kys;
-                if (ky >= N) continue;
-                float* o = a.out + (size_t)c * a.nprod * NN + (size_t)ky * N + kx;
-                o[0] = (a.accumulate ? o[0] : 0.f) + axx[j];
-                if (a.nprod == 4) {
-                    o[NN] = (a.accumulate ? o[NN] : 0.f) + ayy[j];
-                    o[2 * NN] = (a.accumulate ? o[2 * NN] : 0.f) + arx[j];
-                    o[3 * NN] = (a.accumulate ? o[3 * NN] : 0.f) + aix[j];
-                }
-            }
-        }
+        // ---- images (the whole block)
+        if (a.sub == 0) store_images(0);
     }
 }
 
@@ -236,6 +245,8 @@ epic_status fused_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     a.accumulate = accumulate ? 1 : 0;
     a.box_x = p->box_max_x;
     a.box_y = p->box_max_y;
+    a.bits = p->bits;
+    a.sub = p->sub;
     const size_t bytes = sizeof(float2) * fused_smem_elems(a.N, a.A, a.P, a.SW, a.box_x, a.box_y);
     const int items = a.C * a.n_s;
     const int grid = std::min(items, p->sm_count);

@@ -176,6 +176,10 @@ extern "C" epic_status epic_image_static_scratch(epic_plan_t p, const uint8_t* v
     }
     const int C = p->C, P = p->P, N = p->N, A = p->A;
     const size_t per_t = (size_t)C * P * N * N * sizeof(float2);
+    if (p->bits != 4 || p->sub != 0) {
+        p->last_error = "static-scratch imaging: 4+4-bit input and whole-block images only";
+        return EPIC_ERR_UNSUPPORTED;
+    }
     if (per_t > kStaticScratchBytes) {
         p->last_error = "static-scratch imaging: one time sample needs " + std::to_string(per_t >> 20) +
                         " MiB of grid scratch (channels x pols x N^2 x 8 bytes); the static scratch holds " +

@@ -21,7 +21,7 @@ constexpr int kColTile = 16;
 constexpr size_t kGridBudget = 512ull << 20;  // bytes of the chunk grid buffer
 
 __global__ void __launch_bounds__(kThreads) k_plain_grid(const uint8_t* __restrict__ volt, int t0, int C, int A,
-                                                         int P, int N, const int4* __restrict__ box,
+                                                         int P, int N, int bits, const int4* __restrict__ box,
                                                          const int* __restrict__ cell_off,
                                                          const int* __restrict__ cell_ptr,
                                                          const int* __restrict__ ce, const float2* __restrict__ cw,
@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid(const uint8_t* __restri
 {
     extern __shared__ float2 sv[];  // [A][P] unpacked voltages of this frame
     const int tl = blockIdx.x, c = blockIdx.y;
-    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
-    for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = unpack44(fr[i]);
+    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P * (bits / 4);
+    for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = load_sample(fr, i, bits);
     __syncthreads();
     const int4 b = box[c];
     const int* ptr = cell_ptr + cell_off[c];
@@ -59,14 +59,14 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid(const uint8_t* __restri
 // (very large arrays): each contribution reads and unpacks its voltage byte
 // through the read-only data cache.
 __global__ void __launch_bounds__(kThreads) k_plain_grid_g(const uint8_t* __restrict__ volt, int t0, int C, int A,
-                                                           int P, int N, const int4* __restrict__ box,
+                                                           int P, int N, int bits, const int4* __restrict__ box,
                                                            const int* __restrict__ cell_off,
                                                            const int* __restrict__ cell_ptr,
                                                            const int* __restrict__ ce, const float2* __restrict__ cw,
                                                            float2* __restrict__ grid)
 {
     const int tl = blockIdx.x, c = blockIdx.y;
-    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P;
+    const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P * (bits / 4);
     const int4 b = box[c];
     const int* ptr = cell_ptr + cell_off[c];
     const size_t NN = (size_t)N * N;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid_g(const uint8_t* __rest
             for (int q = ptr[r]; q < q1; ++q) {
                 const int e = ce[q];
                 const float2 w = cw[q];
-                a0 = cfma(w, unpack44(__ldg(fr + (size_t)e * P)), a0);
-                if (P == 2) a1 = cfma(w, unpack44(__ldg(fr + (size_t)e * P + 1)), a1);
+                a0 = cfma(w, load_sample(fr, (size_t)e * P, bits), a0);
+                if (P == 2) a1 = cfma(w, load_sample(fr, (size_t)e * P + 1, bits), a1);
             }
         }
         g[cell] = a0;
@@ -134,15 +134,21 @@ __global__ void __launch_bounds__(kThreads) k_plain_fft_cols(float2* __restrict_
     }
 }
 
+// Products summed over the chunk's frames (sub = 0), or over each interval of sub
+// frames (sub-integrations, paper Sec. 4): interval k of the chunk goes to image
+// set out_iv0 + k.
 __global__ void __launch_bounds__(kThreads) k_plain_sqacc(const float2* __restrict__ grid, int nt, int C, int P, int N,
-                                                          float* __restrict__ out, int accumulate)
+                                                          float* __restrict__ out, int accumulate, int sub, int out_iv0)
 {
     const size_t NN = (size_t)N * N;
     const size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (pix >= NN) return;
+    const int nprod = P == 2 ? 4 : 1;
+    const int span = sub > 0 ? sub : nt;
+    for (int iv = 0; iv * span < nt; ++iv) {
     float xx = 0.f, yy = 0.f, rxy = 0.f, ixy = 0.f;
-    for (int tl = 0; tl < nt; ++tl) {
+    for (int tl = iv * span; tl < (iv + 1) * span; ++tl) {
         const float2* g = grid + ((size_t)tl * C + c) * P * NN;
         const float2 X = g[pix];
         xx = fmaf(X.x, X.x, fmaf(X.y, X.y, xx));
@@ -153,14 +159,14 @@ __global__ void __launch_bounds__(kThreads) k_plain_sqacc(const float2* __restri
             ixy = fmaf(X.y, Y.x, fmaf(-X.x, Y.y, ixy));
         }
     }
-    const int nprod = P == 2 ? 4 : 1;
-    float* o = out + (size_t)c * nprod * NN + pix;
+    float* o = out + ((size_t)(out_iv0 + iv) * C + c) * nprod * NN + pix;
     if (accumulate) {
         o[0] += xx;
         if (P == 2) { o[NN] += yy; o[2 * NN] += rxy; o[3 * NN] += ixy; }
     } else {
         o[0] = xx;
         if (P == 2) { o[NN] = yy; o[2 * NN] = rxy; o[3 * NN] = ixy; }
+    }
     }
 }
 
@@ -179,7 +185,8 @@ size_t cols_smem(int N) { return sizeof(float2) * ((size_t)N / 2 + 2ull * col_ti
 epic_status plain_set_chunk(epic_plan_s* p, size_t budget)
 {
     const size_t per_t = (size_t)p->C * p->P * p->N * p->N * sizeof(float2);
-    const int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    if (p->sub > 0) tcn = std::max(p->sub, tcn - tcn % p->sub);  // whole sub-integrations per chunk
     const size_t bytes = per_t * tcn;
     p->chunk_budget = budget;
     if (p->scratch && bytes == p->scratch_bytes) {
@@ -218,14 +225,15 @@ epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     const int C = p->C, P = p->P, N = p->N, A = p->A;
     float2* grid = (float2*)p->scratch;
     const size_t sg = sizeof(float2) * (size_t)A * P;
+    const int bits = p->bits;
     for (int t0 = 0; t0 < T; t0 += p->time_chunk) {
         const int nt = std::min(p->time_chunk, T - t0);
         ev_begin(p, "k_plain_grid", s);
         if ((int)sg <= p->smem_optin)
-            k_plain_grid<<<dim3(nt, C), kThreads, sg, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off,
+            k_plain_grid<<<dim3(nt, C), kThreads, sg, s>>>(volt, t0, C, A, P, N, bits, p->dt.box, p->dt.cell_off,
                                                            p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
         else
-            k_plain_grid_g<<<dim3(nt, C), kThreads, 0, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off,
+            k_plain_grid_g<<<dim3(nt, C), kThreads, 0, s>>>(volt, t0, C, A, P, N, bits, p->dt.box, p->dt.cell_off,
                                                             p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
         ev_end(p, s);
         const size_t n_rows = (size_t)nt * C * P * N;
@@ -240,7 +248,8 @@ epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
         ev_end(p, s);
         ev_begin(p, "k_plain_sqacc", s);
         k_plain_sqacc<<<dim3((unsigned)(((size_t)N * N + kThreads - 1) / kThreads), C), kThreads, 0, s>>>(
-            grid, nt, C, P, N, out, (accumulate || t0 > 0) ? 1 : 0);
+            grid, nt, C, P, N, out, (accumulate || (t0 > 0 && p->sub == 0)) ? 1 : 0, p->sub,
+            p->sub > 0 ? t0 / p->sub : 0);
         ev_end(p, s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(p, e, "plain path launch");

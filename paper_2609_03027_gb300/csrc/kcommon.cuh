@@ -15,6 +15,17 @@ __device__ __forceinline__ float2 unpack44(uint32_t b)
     return make_float2((float)re, (float)im);
 }
 
+// Complex sample idx (= element * P + pol) of one frame: a 4+4-bit byte (bits 4) or a
+// real byte followed by an imaginary byte (bits 8, paper Sec. 4), two's complement.
+__device__ __forceinline__ float2 load_sample(const uint8_t* frame, size_t idx, int bits)
+{
+    if (bits == 8) {
+        const char2 v = *reinterpret_cast<const char2*>(frame + 2 * idx);
+        return make_float2((float)v.x, (float)v.y);
+    }
+    return unpack44(frame[idx]);
+}
+
 // acc + w * v for complex numbers.
 __device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc)
 {

@@ -242,7 +242,7 @@ epic_status epic_server_submit(epic_server_t s, epic_plan_t plan, const uint8_t*
     if (!s || !plan || !out_dev || !ticket || T < 0 || T > plan->max_time || (T > 0 && !volt_host) ||
         (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)))
         return EPIC_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)T * plan->C * plan->A * plan->P;
+    const size_t bytes = (size_t)T * plan->C * plan->A * plan->P * (plan->bits / 4);
     if (round_up(bytes) > s->pool_bytes) return EPIC_ERR_OOM;
     Job* j = new (std::nothrow) Job();
     if (!j) return EPIC_ERR_OOM;

@@ -59,7 +59,8 @@ class _PlanDesc(ctypes.Structure):
     _fields_ = [("n_ant", ctypes.c_int), ("pos_m", ctypes.POINTER(ctypes.c_double)), ("n_pol", ctypes.c_int),
                 ("n_chan", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("cell_m", ctypes.POINTER(ctypes.c_double)), ("grid_n", ctypes.c_int), ("gcf", _Gcf),
-                ("path", ctypes.c_int), ("max_time", ctypes.c_int)]
+                ("path", ctypes.c_int), ("max_time", ctypes.c_int), ("input_bits", ctypes.c_int),
+                ("sub_int", ctypes.c_int)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -71,7 +72,7 @@ class _PlanInfo(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("n_prod", ctypes.c_int), ("box_max_x", ctypes.c_int),
                 ("box_max_y", ctypes.c_int), ("time_chunk", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int),
-                ("gemm_flops_per_sample", ctypes.c_double)]
+                ("gemm_flops_per_sample", ctypes.c_double), ("input_bits", ctypes.c_int), ("sub_int", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -155,7 +156,7 @@ class Plan:
 
     def __init__(self, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int, sigma_cells: float = 1.0,
                  f_ref_hz: Optional[float] = None, freq_scaled: bool = False, cell_m=None, path: str = "auto",
-                 max_time: int = 1024, gcf_table=None, oversample: int = 1):
+                 max_time: int = 1024, gcf_table=None, oversample: int = 1, input_bits: int = 4, sub_int: int = 0):
         self._lib = load()
         self.pos = np.ascontiguousarray(pos_m, dtype=np.float64).reshape(-1, 2)
         self.freq = np.ascontiguousarray(freq_hz, dtype=np.float64).ravel()
@@ -164,6 +165,9 @@ class Plan:
         self.n_ant, self.n_chan, self.n_pol, self.grid_n = self.pos.shape[0], self.freq.shape[0], int(n_pol), int(grid_n)
         self.n_prod = 1 if self.n_pol == 1 else 4
         self.max_time = int(max_time)
+        self.input_bits = int(input_bits)
+        self.sub_int = int(sub_int)
+        self._sample = (2,) if self.input_bits == 8 else ()      # trailing byte-pair axis of 8+8-bit input
         d = _PlanDesc()
         d.n_ant = self.n_ant
         d.pos_m = self.pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -181,6 +185,8 @@ class Plan:
         d.gcf.table = None if self.table is None else self.table.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         d.path = PATHS[path] if isinstance(path, str) else int(path)
         d.max_time = self.max_time
+        d.input_bits = self.input_bits
+        d.sub_int = self.sub_int
         h = ctypes.c_void_p()
         _check(self._lib, self._lib.epic_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -188,7 +194,13 @@ class Plan:
     @classmethod
     def from_config(cls, cfg, path: str = "auto", max_time: Optional[int] = None) -> "Plan":
         return cls(cfg.pos_m, cfg.freq_hz, cfg.n_pol, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells, cfg.f_ref_hz,
-                   cfg.freq_scaled, None, path, cfg.n_time if max_time is None else max_time)
+                   cfg.freq_scaled, None, path, cfg.n_time if max_time is None else max_time,
+                   input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0))
+
+    def image_shape(self, T: int):
+        """Shape of the images of a T-sample block (image sets x C x n_prod x N x N with sub-integrations)."""
+        base = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        return ((T // self.sub_int,) + base) if self.sub_int > 0 else base
 
     # ------------------------------------------------------------------ calls
     def _handle(self):
@@ -204,9 +216,10 @@ class Plan:
         import torch
         if not (isinstance(volt, torch.Tensor) and volt.is_cuda and volt.dtype == torch.uint8):
             raise TypeError("volt must be a CUDA uint8 tensor [T][C][A][P]")
-        if not volt.is_contiguous() or volt.dim() != 4 or tuple(volt.shape[1:]) != (self.n_chan, self.n_ant, self.n_pol):
-            raise ValueError(f"volt must be contiguous [T][{self.n_chan}][{self.n_ant}][{self.n_pol}]")
-        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        want = (self.n_chan, self.n_ant, self.n_pol) + self._sample
+        if not volt.is_contiguous() or volt.dim() != 1 + len(want) or tuple(volt.shape[1:]) != want:
+            raise ValueError(f"volt must be contiguous [T]{list(want)}")
+        shape = self.image_shape(int(volt.shape[0]))
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device=volt.device)
         elif tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
@@ -222,11 +235,12 @@ class Plan:
                    stream=None, time_kernels: bool = False) -> np.ndarray:
         """Host-buffer call: H2D copy, imaging, D2H copy, stream synchronised on return."""
         v = np.asarray(volt)
-        if v.dtype != np.uint8 or v.ndim != 4 or v.shape[1:] != (self.n_chan, self.n_ant, self.n_pol):
-            raise ValueError("volt must be uint8 [T][C][A][P]")
+        want = (self.n_chan, self.n_ant, self.n_pol) + self._sample
+        if v.dtype != np.uint8 or v.ndim != 1 + len(want) or v.shape[1:] != want:
+            raise ValueError(f"volt must be uint8 [T]{list(want)}")
         if not v.flags.c_contiguous:
             raise ValueError("volt must be C-contiguous")
-        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        shape = self.image_shape(int(v.shape[0]))
         if out is None:
             out = np.zeros(shape, dtype=np.float32)
         if out.shape != shape or out.dtype != np.float32 or not out.flags.c_contiguous:
@@ -249,7 +263,7 @@ class Plan:
         import torch
         if not (isinstance(volt, torch.Tensor) and volt.is_cuda and volt.dtype == torch.uint8 and volt.is_contiguous()):
             raise TypeError("volt must be a contiguous CUDA uint8 tensor [T][C][A][P]")
-        shape = (self.n_chan, self.n_prod, self.grid_n, self.grid_n)
+        shape = self.image_shape(int(volt.shape[0]))
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device=volt.device)
         rep = _TuneReport()
@@ -323,8 +337,9 @@ class Server:
     def submit(self, plan: "Plan", volt: np.ndarray, out, accumulate: bool = False) -> Optional[int]:
         """Queue a host block; returns a ticket, or None when the server is busy."""
         v = np.ascontiguousarray(volt, dtype=np.uint8)
-        if v.ndim != 4 or v.shape[1:] != (plan.n_chan, plan.n_ant, plan.n_pol):
-            raise ValueError("block must be uint8 [T][C][A][P] of the plan")
+        want = (plan.n_chan, plan.n_ant, plan.n_pol) + plan._sample
+        if v.ndim != 1 + len(want) or v.shape[1:] != want:
+            raise ValueError(f"block must be uint8 [T]{list(want)} of the plan")
         t = ctypes.c_uint64()
         st = self._lib.epic_server_submit(self._h, plan._handle(), v.ctypes.data if v.shape[0] else None,
                                           int(v.shape[0]), out.data_ptr(), ACCUMULATE if accumulate else RESET,

@@ -197,3 +197,31 @@ def test_large_grid_workload_plain_sampled():
     v = synth.make_voltages(cfg)
     got = run_gpu(cfg, v, "plain")
     assert_parity(got, oracle_image(cfg, v), "plain", cfg.name)
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+@pytest.mark.parametrize("bits,sub", [(8, 0), (8, 4), (4, 2), (8, 1)])
+def test_eight_bit_input_and_sub_integrations(path, bits, sub):
+    # 8+8-bit voltages and high-cadence sub-integrations (paper Sec. 4): one image set per
+    # `sub` samples, each matching the oracle's; a T = 0 call and a wrong T are handled
+    cfg = dataclasses.replace(synth.small_config(n_ant=36, n_chan=3, n_pol=2, grid_n=32, gcf_k=3, n_time=12,
+                                                 seed=51 + bits + sub, diameter_m=9.0, sigma=0.7),
+                              input_bits=bits, sub_int=sub)
+    v = synth.make_voltages(cfg)
+    ref = oracle_image(cfg, v)
+    with E.Plan.from_config(cfg, path=path) as plan:
+        d = torch.from_numpy(v).cuda()
+        got = plan.image(d).cpu().numpy()
+        assert got.shape == ref.shape
+        if sub:
+            for k in range(ref.shape[0]):
+                assert_parity(got[k], ref[k], path, f"bits={bits} sub={sub} set {k}")
+            acc = plan.image(d, out=torch.from_numpy(got).cuda(), accumulate=True).cpu().numpy()
+            assert_parity(acc[1] / 2, ref[1], path, "accumulated sub-integration")
+            if sub > 1:
+                with pytest.raises(E.EpicError):
+                    plan.image(d[:sub + 1].contiguous())
+        else:
+            assert_parity(got, ref, path, f"bits={bits}")
+        host = plan.image_host(v)
+        assert np.array_equal(host, got)
