@@ -361,6 +361,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the streaming-mix serving run (0 = skip)")
+    ap.add_argument("--input-bits", type=int, default=4, choices=[4, 8], help="voltage sample format")
+    ap.add_argument("--sub-int", type=int, default=0, help="samples per image set (0 = whole block)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -368,6 +370,8 @@ def main():
     cfg = synth.config(args.config)
     if args.time > 0:
         cfg.n_time = args.time
+    cfg.input_bits = args.input_bits
+    cfg.sub_int = args.sub_int
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
         return
@@ -382,7 +386,8 @@ def main():
     volt = synth.make_voltages(cfg)
     units = cfg.pixel_updates(T)
     d_volt = torch.from_numpy(volt).to(dev)
-    out = torch.empty((cfg.n_chan, cfg.n_prod, cfg.grid_n, cfg.grid_n), dtype=torch.float32, device=dev)
+    sets = (T // cfg.sub_int,) if cfg.sub_int > 0 else ()
+    out = torch.empty(sets + (cfg.n_chan, cfg.n_prod, cfg.grid_n, cfg.grid_n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -481,7 +486,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.config], "path": info.get("path_name", args.path),
+                "config": {"workload": WORKLOADS[args.config] + ("" if cfg.input_bits == 4 else ", 8+8-bit input")
+                           + (f", image set every {cfg.sub_int} samples" if cfg.sub_int else ""),
+                           "path": info.get("path_name", args.path),
                            "global_batch_pixel_updates": units * world, "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "launch": "cuda-graph" if use_graph else "per-kernel",
