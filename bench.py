@@ -224,16 +224,18 @@ def run_reference(args, cfg, world, rank):
 
 # ----------------------------------------------------------------------------- traffic record
 
-def recorded_traffic(kernel: str, workload: int, samples: int):
+def recorded_traffic(kernel: str, workload: int, samples: int, cfg, params):
     """DRAM bytes of one launch processing `samples` time samples, from the committed ncu
-    summary (profiles/traffic.json: bytes per sample of one capture), if the kernel source
-    is unchanged since the capture; None otherwise."""
+    summary (profiles/traffic.json: bytes per sample of one capture), if the kernel source,
+    the input format and the plan parameters are those of the capture; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or cfg.input_bits != 4 or cfg.sub_int:
         return None
     key = "k_dftgemm_grid" if kernel.startswith("k_dftgemm_grid") else kernel
     rec = json.load(open(path)).get(f"{key}@cfg{workload}")
     if not rec:
+        return None
+    if any((params or {}).get(k) != v for k, v in rec.get("params", {}).items()):
         return None
     src = os.path.join(ROOT, "paper_2609_03027_gb300", "csrc", rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["sha"]:
@@ -358,6 +360,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time", type=int, default=0, help="override the block length T (small profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (plan defaults)")
+    ap.add_argument("--params", default="", help="tuning parameters to set instead of tuning, e.g. split=1,chunk_mb=768")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the streaming-mix serving run (0 = skip)")
@@ -395,7 +398,13 @@ def main():
 
     def time_path(path, steps, warmup, sample_clocks=False):
         plan = E.Plan.from_config(cfg, path=path, max_time=T)
-        tuning = None if args.no_tune else plan.tune(d_volt, out=out, reps=2)
+        if args.params and path == args.path:
+            fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.params.split(","))}
+            for k, v in fixed.items():
+                plan.set_param(k, v)
+            tuning = {"params": fixed}
+        else:
+            tuning = None if args.no_tune else plan.tune(d_volt, out=out, reps=2)
         info = plan.info()
         if tuning is not None:
             info["tuning"] = tuning["params"]
@@ -453,7 +462,7 @@ def main():
         peak, unit = pk["hbm_gbs"], "GB/s"
     roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak,
-            "traffic": recorded_traffic(dom, args.config, int(round(T / per_step_launches))),
+            "traffic": recorded_traffic(dom, args.config, int(round(T / per_step_launches)), cfg, info.get("tuning")),
             "peak_source": pk["source"] if bound != "alu" else "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
             "kernel_ms": kavg_ms, "launches_per_step": per_step_launches,
             "kernel_share": sum(ktimes[dom]) / sum(sum(v) for v in ktimes.values())}

@@ -66,6 +66,11 @@ def test_every_byte_code_including_minus_eight(path):
     v = synth.random_bytes((8, 2, 64, 2), seed=3)
     assert set(np.unique(v)) == set(range(256))
     assert_parity(run_gpu(cfg, v, path), oracle_image(cfg, v), path, "all codes")
+    # 8+8-bit: every real and imaginary byte, including -128
+    cfg8 = dataclasses.replace(cfg, input_bits=8)
+    v8 = synth.random_bytes((8, 2, 64, 2, 2), seed=4)
+    assert set(np.unique(v8[..., 0])) == set(range(256)) == set(np.unique(v8[..., 1]))
+    assert_parity(run_gpu(cfg8, v8, path), oracle_image(cfg8, v8), path, "all 8-bit codes")
 
 
 @pytest.mark.parametrize("path", GPU_PATHS)
