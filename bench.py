@@ -229,7 +229,7 @@ def recorded_traffic(kernel: str, workload: int, samples: int, cfg, params):
     summary (profiles/traffic.json: bytes per sample of one capture), if the kernel source,
     the input format and the plan parameters are those of the capture; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path) or cfg.input_bits != 4 or cfg.sub_int:
+    if not os.path.exists(path) or cfg.input_bits != 4 or cfg.sub_int or cfg.jones is not None:
         return None
     key = "k_dftgemm_grid" if kernel.startswith("k_dftgemm_grid") else kernel
     rec = json.load(open(path)).get(f"{key}@cfg{workload}")
@@ -366,6 +366,8 @@ def main():
                     help="length of the streaming-mix serving run (0 = skip)")
     ap.add_argument("--input-bits", type=int, default=4, choices=[4, 8], help="voltage sample format")
     ap.add_argument("--sub-int", type=int, default=0, help="samples per image set (0 = whole block)")
+    ap.add_argument("--pol-mix", action="store_true",
+                    help="per-element polarisation-mixing kernels (seeded random 2x2 gains and leakage)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -375,6 +377,8 @@ def main():
         cfg.n_time = args.time
     cfg.input_bits = args.input_bits
     cfg.sub_int = args.sub_int
+    if args.pol_mix:
+        cfg.jones = synth.make_jones(cfg, seed=cfg.seed)
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
         return
@@ -496,7 +500,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config] + ("" if cfg.input_bits == 4 else ", 8+8-bit input")
-                           + (f", image set every {cfg.sub_int} samples" if cfg.sub_int else ""),
+                           + (f", image set every {cfg.sub_int} samples" if cfg.sub_int else "")
+                           + (", per-element polarisation mixing" if cfg.jones is not None else ""),
                            "path": info.get("path_name", args.path),
                            "global_batch_pixel_updates": units * world, "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -54,6 +54,7 @@ class EpicConfig:
     seed: int
     input_bits: int = 4        # 4: 4+4-bit bytes; 8: 8+8-bit (real byte, imaginary byte)
     sub_int: int = 0           # time samples per output image (0 = the whole block)
+    jones: Optional[np.ndarray] = None  # complex [C][A][2][2] polarisation mixing J^{ap}, None = none
 
     @property
     def n_ant(self) -> int:
@@ -230,6 +231,24 @@ def make_voltages(cfg: EpicConfig, t0: int = 0, n_time: Optional[int] = None,
         else:
             out[i] = pack_nibbles(np.clip(np.rint(re), -7, 7), np.clip(np.rint(im), -7, 7))
     return out
+
+
+def make_jones(cfg: EpicConfig, seed: int = 0, gain_rms: float = 0.1, leak_rms: float = 0.05) -> np.ndarray:
+    """complex128 [C][A][2][2] direction-independent polarisation-mixing matrices per
+    element and channel, J = [[g_X, d_XY], [d_YX, g_Y]]: complex gains g_p = (1 + a) e^{i phi}
+    with a ~ N(0, gain_rms), phi ~ U(-pi, pi), and leakage terms d ~ CN(0, leak_rms^2),
+    drawn independently per (channel, element) from the stream [seed, 9_000_000]."""
+    rng = np.random.default_rng([seed, 9_000_000])
+    C, A = cfg.n_chan, cfg.n_ant
+    J = np.zeros((C, A, 2, 2), dtype=np.complex128)
+    amp = 1.0 + gain_rms * rng.standard_normal((C, A, 2))
+    phi = rng.uniform(-math.pi, math.pi, (C, A, 2))
+    J[:, :, 0, 0] = amp[..., 0] * np.exp(1j * phi[..., 0])
+    J[:, :, 1, 1] = amp[..., 1] * np.exp(1j * phi[..., 1])
+    d = (rng.standard_normal((C, A, 2)) + 1j * rng.standard_normal((C, A, 2))) * (leak_rms / math.sqrt(2.0))
+    J[:, :, 0, 1] = d[..., 0]
+    J[:, :, 1, 0] = d[..., 1]
+    return J
 
 
 def random_bytes(shape: Tuple[int, ...], seed: int) -> np.ndarray:

@@ -108,6 +108,13 @@ typedef struct {
                                S > 0: one image set per S samples (sub-integrations, Sec. 4) --
                                T of every call a multiple of S, 1 <= S <= max_time; the tensor
                                path needs its control-warp kernel for it (UNSUPPORTED otherwise) */
+    const float* jones;     /* NULL: no polarisation mixing (W_e^{ap} = delta_ap W).  Otherwise host
+                               [n_chan][n_ant][2][2] complex float pairs J_{c,e}^{ap} (output pol a,
+                               input pol p), copied: the per-element kernel of Eq. 1 is
+                               W_e^{ap}(r) = J_{c,e}^{ap} W(r), a direction-independent 2x2
+                               leakage/gain matrix per element and channel times the shared GCF,
+                               so output pol a grids sum_p conj(J^{ap}) E^p.  Needs n_pol == 2;
+                               every value finite (INVALID_ARG otherwise)                          */
 } epic_plan_desc;
 
 typedef struct epic_plan_s* epic_plan_t;
@@ -127,6 +134,7 @@ typedef struct {
                                      the occupied box); 0 for the FFT paths                        */
     int input_bits;         /* 4 or 8                                                             */
     int sub_int;            /* samples per image set, 0 = the whole block                         */
+    int pol_mix;            /* 1 when the plan has a polarisation-mixing kernel (jones)           */
 } epic_plan_info;
 
 /* flags of epic_image / epic_image_host */
@@ -235,7 +243,8 @@ epic_status epic_device_query(int* sm_count, int* smem_optin_bytes, int* cc_majo
  * counterpart; it runs the plain FP32 pipeline (grid, row FFT, column FFT,
  * products) in time chunks that fit the array, with any plan.
  * - EPIC_ERR_UNSUPPORTED (with the sizes in epic_last_error) when one time sample
- *   of the plan needs more than 32 MiB of grids (n_chan x n_pol x N^2 x 8 bytes).
+ *   of the plan needs more than 32 MiB of grids (n_chan x n_pol x N^2 x 8 bytes),
+ *   and for plans with 8+8-bit input, sub-integrations or polarisation mixing.
  * - The first call on a device looks up the array's device address and sets the
  *   kernels' shared-memory limits there; make that first call before any stream
  *   capture.

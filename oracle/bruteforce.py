@@ -89,12 +89,22 @@ def footprint_xcorr(wd: np.ndarray) -> np.ndarray:
 
 
 def image(volt: np.ndarray, pos_m, freq_hz, n_pol, grid_n, gcf_k, sigma_cells, f_ref_hz=1.0,
-          freq_scaled=False, cell_m=None, table=None, oversample=1) -> np.ndarray:
-    """float64[C][nprod][N][N] through visibilities (same output convention as the oracle)."""
+          freq_scaled=False, cell_m=None, table=None, oversample=1, jones=None, input_bits=4) -> np.ndarray:
+    """float64[C][nprod][N][N] through visibilities (same output convention as the oracle).
+
+    jones (complex [C][A][2][2], optional): element kernels J_e^{ap} W(r).  Because such a
+    kernel factors into a matrix per element and the shared W, the correlator sees the
+    element's voltages after mixing, sum_p conj(J^{ap}) E^p, and grids with W as before."""
     v = np.asarray(volt)
-    T, C, A, P = v.shape
+    if input_bits == 8:                                          # (real, imaginary) int8 pairs
+        b = v.view(np.int8).astype(np.int64)
+        E = b[..., 0] + 1j * b[..., 1]
+    else:
+        E = decode_nibbles(v)                                    # [T][C][A][P]
+    T, C, A, P = E.shape
     N = grid_n
-    E = decode_nibbles(v)                                        # [T][C][A][P]
+    if jones is not None:
+        E = np.einsum("caqp,tcap->tcaq", np.conj(np.asarray(jones, dtype=np.complex128)), E)
     kk = np.arange(N)
     D = np.exp(2j * math.pi * np.outer(kk, kk) / N)              # D[k][d], + sign
     shift = (np.arange(N) + N // 2) % N                          # image index -> Fourier index

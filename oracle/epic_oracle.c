@@ -15,7 +15,9 @@
  *          of the polarisations, averaged (here: summed) over the integration.
  *
  * Readings taken where the paper is silent (each is also listed in the design notes):
- *   - W^{ap} = delta_{ap} W: one GCF per element shared by both pols, no pol mixing.
+ *   - W^{ap} = delta_{ap} W (one GCF shared by both pols, no pol mixing) unless a mixing
+ *     kernel is given; then W_e^{ap}(r) = J_e^{ap} W(r) with a complex 2x2 J per element
+ *     and channel (direction-independent leakage; eo_grid_mix takes Eq. 1's double sum).
  *   - Grid spacing Delta_c = lambda_c/2 unless given; element cell coordinates are
  *     u = (x - xbar)/Delta + N/2, v = (y - ybar)/Delta + N/2 with (xbar, ybar) the
  *     array centroid; grid point j sits at integer cell j.
@@ -201,6 +203,40 @@ static void eo_grid(int n_ant, int K, int N, const int* tap_x, const int* tap_y,
     }
 }
 
+/* ---- gridding with a polarisation-mixing kernel (Eq. 1 in full) ----------------
+ * Output pol a of one dual-pol frame: G^a[j] = sum_e sum_p conj(W_e^{ap}(r_j - r_e)) E_e^p,
+ * the element kernel being W_e^{ap}(r) = J_e^{ap} W(r) with J_e a complex 2x2 matrix
+ * (jones_c: [A][2][2][2] doubles, J^{ap} of element e at ((e * 2 + a) * 2 + p) * 2) and w
+ * holding conj(W) per tap.  Each tap of each element applies both of its kernel entries
+ * conj(J^{ap}) conj(W) to the two input pols, as the double sum reads. */
+static void eo_grid_mix(int n_ant, int K, int N, const int* tap_x, const int* tap_y, const double* w,
+                        const uint8_t* frame, int a, int bits, const double* jones_c, double* g)
+{
+    memset(g, 0, sizeof(double) * 2 * (size_t)N * N);
+    for (int e = 0; e < n_ant; ++e) {
+        int vr[2], vi[2];
+        for (int p = 0; p < 2; ++p) {
+            if (bits == 8) eo_unpack8(frame + 2 * ((size_t)e * 2 + p), &vr[p], &vi[p]);
+            else eo_unpack(frame[e * 2 + p], &vr[p], &vi[p]);
+        }
+        for (int ty = 0; ty < K; ++ty) {
+            for (int tx = 0; tx < K; ++tx) {
+                const double* c = w + (((size_t)e * K + ty) * K + tx) * 2;   /* conj(W) */
+                int jx = tap_x[e * K + tx], jy = tap_y[e * K + ty];
+                double* o = g + ((size_t)jy * N + jx) * 2;
+                for (int p = 0; p < 2; ++p) {
+                    const double* J = jones_c + (((size_t)e * 2 + a) * 2 + p) * 2;
+                    /* conj(J W) = conj(J) conj(W) */
+                    const double kr = J[0] * c[0] + J[1] * c[1];
+                    const double ki = J[0] * c[1] - J[1] * c[0];
+                    o[0] += kr * vr[p] - ki * vi[p];
+                    o[1] += kr * vi[p] + ki * vr[p];
+                }
+            }
+        }
+    }
+}
+
 /* Grid one frame (exposed for transform-level checks such as Parseval). */
 int eo_grid_frame(int n_ant, const double* pos_m, int n_pol, int n_chan, const double* freq_hz,
                   const double* cell_m, int N, int gcf_kind, int K, double sigma_cells, double f_ref_hz,
@@ -228,16 +264,19 @@ int eo_grid_frame(int n_ant, const double* pos_m, int n_pol, int n_chan, const d
 /* volt: uint8[T][n_chan][A][P] (bits = 4: one byte per sample) or uint8[T][n_chan][A][P][2]
  * (bits = 8: real byte, imaginary byte); chans: n_sel channel indices (NULL = all);
  * sub: time samples per output image (0 = one image set for the whole block; T a multiple of sub);
+ * jones: NULL (W_e^{ap} = delta_ap W) or double[n_chan][A][2][2][2], the complex 2x2 polarisation-
+ * mixing matrix J^{ap} of each element and channel (n_pol = 2; see eo_grid_mix);
  * out: double[n_int][n_sel][nprod][N][N] with n_int = T / sub (1 when sub = 0) and nprod = 1
  * (P = 1) or 4 (XX, YY, Re XY, Im XY): Eq. 2's average taken (as a sum) over each interval. */
 int eo_image_ext(int n_ant, const double* pos_m, int n_pol, int n_chan, const double* freq_hz,
                  const double* cell_m, int N, int gcf_kind, int K, double sigma_cells, double f_ref_hz,
                  int freq_scaled, int oversample, const float* table,
-                 const uint8_t* volt, int T, int bits, int sub, int n_sel, const int* chans, double* out,
-                 int n_threads)
+                 const uint8_t* volt, int T, int bits, int sub, const double* jones, int n_sel, const int* chans,
+                 double* out, int n_threads)
 {
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || n_chan < 1 || N < 2 || (N & (N - 1)) || K < 1 ||
-        T < 0 || n_sel < 0 || (bits != 4 && bits != 8) || sub < 0 || (sub > 0 && T % sub != 0))
+        T < 0 || n_sel < 0 || (bits != 4 && bits != 8) || sub < 0 || (sub > 0 && T % sub != 0) ||
+        (jones && n_pol != 2))
         return EO_ERR_ARG;
     if (!chans) n_sel = n_chan;
     int nprod = n_pol == 1 ? 1 : 4;
@@ -271,7 +310,11 @@ int eo_image_ext(int n_ant, const double* pos_m, int n_pol, int n_chan, const do
                     for (int t = iv * span; t < (iv + 1) * span; ++t) {
                         const uint8_t* frame = volt + ((size_t)t * n_chan + c) * (size_t)n_ant * n_pol * bytes;
                         for (int p = 0; p < n_pol; ++p) {
-                            eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, bits, g + p * 2 * NN);
+                            if (jones)
+                                eo_grid_mix(n_ant, K, N, tx, ty, w, frame, p, bits,
+                                            jones + (size_t)c * n_ant * 8, g + p * 2 * NN);
+                            else
+                                eo_grid(n_ant, K, N, tx, ty, w, frame, n_pol, p, bits, g + p * 2 * NN);
                             eo_fft2(g + p * 2 * NN, N);
                         }
                         for (size_t k = 0; k < NN; ++k) {
@@ -308,7 +351,7 @@ int eo_image(int n_ant, const double* pos_m, int n_pol, int n_chan, const double
              const uint8_t* volt, int T, int n_sel, const int* chans, double* out, int n_threads)
 {
     return eo_image_ext(n_ant, pos_m, n_pol, n_chan, freq_hz, cell_m, N, gcf_kind, K, sigma_cells, f_ref_hz,
-                        freq_scaled, oversample, table, volt, T, 4, 0, n_sel, chans, out, n_threads);
+                        freq_scaled, oversample, table, volt, T, 4, 0, NULL, n_sel, chans, out, n_threads);
 }
 
 int eo_max_threads(void)

@@ -56,7 +56,7 @@ def lib():
             L.eo_grid_frame.restype = i
             L.eo_image.argtypes = plan + [P(ctypes.c_uint8), i, i, P(i), P(d), i]
             L.eo_image.restype = i
-            L.eo_image_ext.argtypes = plan + [P(ctypes.c_uint8), i, i, i, i, P(i), P(d), i]
+            L.eo_image_ext.argtypes = plan + [P(ctypes.c_uint8), i, i, i, P(d), i, P(i), P(d), i]
             L.eo_image_ext.restype = i
             L.eo_unpack8.argtypes = [P(ctypes.c_uint8), P(i), P(i)]
             L.eo_unpack8.restype = None
@@ -163,12 +163,13 @@ def grid_frame(volt: np.ndarray, t: int, c: int, p: int, pos_m, freq_hz, n_pol: 
 def image(volt: np.ndarray, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int, sigma_cells: float,
           f_ref_hz: float = 1.0, freq_scaled: bool = False, cell_m=None, chans: Optional[Sequence[int]] = None,
           gcf_kind: int = GCF_GAUSSIAN, oversample: int = 1, table=None, threads: int = 0,
-          input_bits: int = 4, sub_int: int = 0) -> np.ndarray:
+          input_bits: int = 4, sub_int: int = 0, jones=None) -> np.ndarray:
     """Accumulated images of the selected channels: float64[n_sel][nprod][N][N], or with
     sub-integrations (sub_int > 0) float64[T / sub_int][n_sel][nprod][N][N].
 
     volt holds ALL channels: uint8[T][C][A][P] (4+4-bit) or uint8[T][C][A][P][2] (8+8-bit:
-    real byte, imaginary byte); chans selects which are imaged.
+    real byte, imaginary byte); chans selects which are imaged.  jones: optional complex
+    [C][A][2][2] polarisation-mixing matrices J^{ap} (element kernel J^{ap} W(r), Eq. 1).
     """
     geo = _Geom(pos_m, freq_hz, cell_m, n_pol, grid_n, gcf_kind, gcf_k, sigma_cells, f_ref_hz, freq_scaled,
                 oversample, table)
@@ -183,8 +184,15 @@ def image(volt: np.ndarray, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int,
     nprod = 1 if n_pol == 1 else 4
     n_int = T // sub_int if sub_int > 0 else 1
     out = np.zeros((n_int, n_sel, nprod, grid_n, grid_n), dtype=np.float64)
-    rc = lib().eo_image_ext(*geo.args(), _p(v, ctypes.c_uint8), T, int(input_bits), int(sub_int), n_sel,
-                            _p(sel, ctypes.c_int), _p(out, ctypes.c_double), int(threads))
+    jd = None
+    if jones is not None:
+        j = np.asarray(jones)
+        if j.shape != (C, geo.pos.shape[0], 2, 2):
+            raise OracleError("jones must be complex [C][A][2][2]")
+        jd = np.ascontiguousarray(j, dtype=np.complex128).view(np.float64)
+    rc = lib().eo_image_ext(*geo.args(), _p(v, ctypes.c_uint8), T, int(input_bits), int(sub_int),
+                            _p(jd, ctypes.c_double), n_sel, _p(sel, ctypes.c_int), _p(out, ctypes.c_double),
+                            int(threads))
     _check(rc, "image")
     return out if sub_int > 0 else out[0]
 
@@ -193,4 +201,5 @@ def image_cfg(cfg, volt: np.ndarray, chans: Optional[Sequence[int]] = None, thre
     """image() for an ``epic_synth.EpicConfig`` (its input bits and sub-integration)."""
     return image(volt, cfg.pos_m, cfg.freq_hz, cfg.n_pol, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells,
                  cfg.f_ref_hz, cfg.freq_scaled, None, chans, threads=threads,
-                 input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0))
+                 input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0),
+                 jones=getattr(cfg, "jones", None))

@@ -46,6 +46,7 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->dt.twiddle);
     cudaFree(p->dt.first_xy);
     cudaFree(p->dt.w_taps);
+    cudaFree(p->dt.jones);
     cudaFree(p->dt.dft_f16);
     cudaFree(p->tc.a1);
     cudaFree(p->tc.a2);
@@ -208,6 +209,10 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     if (d->input_bits != 0 && d->input_bits != 4 && d->input_bits != 8) return bad("input_bits must be 4 or 8");
     if (d->sub_int < 0 || d->sub_int > d->max_time) return bad("sub_int must be in 0..max_time");
     if ((long long)d->n_ant * d->n_pol > (1 << 20)) return bad("n_ant * n_pol too large");
+    if (d->jones && d->n_pol != 2) return bad("a polarisation-mixing kernel needs n_pol == 2");
+    if (d->jones)
+        for (size_t i = 0; i < (size_t)d->n_chan * d->n_ant * 8; ++i)
+            if (!std::isfinite(d->jones[i])) return bad("jones must be finite");
     for (int c = 0; c < d->n_chan; ++c) {
         if (!(d->freq_hz[c] > 0.0) || !std::isfinite(d->freq_hz[c])) return bad("freq_hz must be > 0 and finite");
         if (d->cell_m && (!(d->cell_m[c] > 0.0) || !std::isfinite(d->cell_m[c]))) return bad("cell_m must be > 0");
@@ -240,6 +245,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
         p->table.assign(d->gcf.table, d->gcf.table + 2 * side * side);
     }
     p->gcf.table = nullptr;
+    if (d->jones) p->jones.assign(d->jones, d->jones + (size_t)d->n_chan * d->n_ant * 8);
 
     std::string err;
     epic_status st = epic::build_geometry(p, &err);
@@ -281,6 +287,12 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     for (size_t i = 0; i < first_xy.size(); ++i) first_xy[i] = (p->first_y[i] << 16) | p->first_x[i];
     std::vector<float2> w_taps(p->w_re.size());
     for (size_t i = 0; i < w_taps.size(); ++i) w_taps[i] = make_float2((float)p->w_re[i], (float)p->w_im[i]);
+    // polarisation mixing rows: entry 2 (c A + e) + a = (conj J^{a0}, conj J^{a1}) of element e, channel c
+    std::vector<float4> jrows(p->jones.size() / 4);
+    for (size_t i = 0; i < jrows.size(); ++i) {
+        const float* j = &p->jones[4 * i];  // J^{a0} re, im, J^{a1} re, im
+        jrows[i] = make_float4(j[0], -j[1], j[2], -j[3]);
+    }
 
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = upload(&p->dt.box, box.data(), box.size(), &p->table_bytes);
@@ -291,6 +303,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     if (e == cudaSuccess) e = upload(&p->dt.twiddle, tw.data(), tw.size(), &p->table_bytes);
     if (e == cudaSuccess) e = upload(&p->dt.first_xy, first_xy.data(), first_xy.size(), &p->table_bytes);
     if (e == cudaSuccess) e = upload(&p->dt.w_taps, w_taps.data(), w_taps.size(), &p->table_bytes);
+    if (e == cudaSuccess) e = upload(&p->dt.jones, jrows.data(), jrows.size(), &p->table_bytes);
     if (e != cudaSuccess) {
         st = epic::cuda_fail(p, e, "plan table upload");
         free_plan(p);
@@ -343,6 +356,7 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
     info->gemm_flops_per_sample = p->path == EPIC_PATH_DFTGEMM_FP16 ? p->tc_flops_per_sample : 0.0;
     info->input_bits = p->bits;
     info->sub_int = p->sub;
+    info->pol_mix = p->jones.empty() ? 0 : 1;
     return EPIC_OK;
 }
 

@@ -27,6 +27,7 @@ struct DeviceTables {
     float2* twiddle = nullptr;    // [N/2] exp(+2 pi i m / N)
     int* first_xy = nullptr;      // [C][A] packed first tap (y << 16 | x)
     float2* w_taps = nullptr;     // [C][A][K][K] weights (conj, shift sign folded)
+    float4* jones = nullptr;      // [C][A][2] polarisation mixing: (conj J^{a0}, conj J^{a1}) per output pol a
     uint16_t* dft_f16 = nullptr;  // DFT-as-GEMM operand tables (tensor path)
     size_t dft_bytes = 0;
 };
@@ -92,6 +93,7 @@ struct epic_plan_s {
     std::vector<double> pos, freq, cell;
     epic_gcf_desc gcf{};
     std::vector<float> table;
+    std::vector<float> jones;             // [C][A][2][2] complex pairs, empty = no polarisation mixing
 
     // host geometry (FP64 computed, stored as used by the kernels)
     std::vector<epic::Box> box;           // [C]

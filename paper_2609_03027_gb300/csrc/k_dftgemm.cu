@@ -186,12 +186,15 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                                                            const int* __restrict__ cell_off,
                                                            const int* __restrict__ cell_ptr,
                                                            const int* __restrict__ ce,
-                                                           const float2* __restrict__ cw, uint8_t* __restrict__ tiles,
+                                                           const float2* __restrict__ cw,
+                                                           const float4* __restrict__ jones,
+                                                           uint8_t* __restrict__ tiles,
                                                            unsigned long long tile_stride)
 {
     extern __shared__ __align__(16) uint8_t gsm[];
     float4* sv = reinterpret_cast<float4*>(gsm);  // [F][A]: (re X, im X, re Y, im Y)
     const int cl = blockIdx.y, c = c0 + cl;
+    const float4* jm = jones ? jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
     const int4 b = box[c];
     const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
     const int* gptr = cell_ptr + cell_off[c];
@@ -216,9 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
         for (int i = threadIdx.x; i < nf * A; i += blockDim.x) {
             const int f = i / A, e = i - f * A;
             const uint8_t* fr = volt + ((size_t)(t0 + tb + f) * C + c) * (size_t)A * P * (bits / 4);
-            const float2 x = load_sample(fr, (size_t)e * P, bits);
-            const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, bits) : make_float2(0.f, 0.f);
-            sv[f * A + e] = make_float4(x.x, x.y, y.x, y.y);
+            sv[f * A + e] = load_quad(fr, e, P, bits, jm);
         }
         __syncthreads();
         for (int task = threadIdx.x; task < tasks; task += blockDim.x) {
@@ -300,6 +301,7 @@ struct GridArgs {
     int max_list;   // largest number of (cell, element) entries of a channel
     int bulk;       // 1: voltage frames copied by the TMA engine (frame bytes % 16 == 0, 16-byte aligned base)
     int bits;       // 4: 4+4-bit bytes, 8: 8+8-bit sample pairs
+    const float4* jones;  // [C][A][2] polarisation-mixing rows (conj J), or nullptr
 };
 
 __host__ __device__ inline size_t grid_ps_smem(int F, int A, int frame_bytes, int max_cells, int max_list, bool cplx)
@@ -361,6 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
         const int c = a.c0 + cl;
         const int4 b = a.box[c];
         const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
+        const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         if (a.bulk && tid == 0 && wn < w1) {  // the other buffer was consumed by the previous pass
             fetch(wn, buf ^ 1);
             pending |= 1u << (buf ^ 1);
@@ -394,17 +397,13 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
-                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
-                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
-                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         } else {
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
-                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
-                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
-                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         }
         __syncthreads();
@@ -566,6 +565,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         const int c = a.c0 + cl;
         const int4 b = a.box[c];
         const int nxp = b.z, nyp = b.w, N1 = P * nyp;
+        const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         const uint32_t tile_bytes = (uint32_t)N1 * pad64(2 * nxp) * 2;
         if (a.bulk && tid == 0 && wn < w1) {
             fetch(wn, buf ^ 1);
@@ -596,17 +596,13 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
-                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
-                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
-                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         } else {
             for (int i = tid; i < nf * A; i += blockDim.x) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
-                const float2 x = load_sample(fr, (size_t)e * P, a.bits);
-                const float2 y = P == 2 ? load_sample(fr, (size_t)e * P + 1, a.bits) : make_float2(0.f, 0.f);
-                sv[fi * A + e] = make_float4(x.x, x.y, y.x, y.y);
+                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         }
         if (tid == 0) tc::bulk_wait_read<1>();  // the stores of the pass before last have read tile buffer tb
@@ -2701,6 +2697,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 g.max_cells = p->tc.grid_max_cells;
                 g.max_list = p->tc.grid_max_list;
                 g.bits = p->bits;
+                g.jones = p->dt.jones;
                 g.bulk = ((A * P * (p->bits / 4)) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
                 const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
                 ev_begin(p, "k_dftgemm_grid", s);
@@ -2739,7 +2736,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->bits,         \
                                                               p->dt.box,                                               \
                                                               p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,         \
-                                                              p->dt.contrib_w, (uint8_t*)p->scratch, p->tc.stride)
+                                                              p->dt.contrib_w, p->dt.jones, (uint8_t*)p->scratch,     \
+                                                              p->tc.stride)
             if (p->tc.grid_csr_smem) {
                 if (F == 4) EPIC_GRID_LAUNCH(true, 4);
                 else if (F == 2) EPIC_GRID_LAUNCH(true, 2);

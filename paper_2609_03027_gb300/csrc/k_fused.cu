@@ -37,6 +37,7 @@ struct FusedArgs {
     int box_x, box_y;  // largest occupied box (for shared-memory carving)
     int bits;          // 4: 4+4-bit bytes, 8: 8+8-bit sample pairs
     int sub;           // samples per output image set (0 = the whole block)
+    const float4* jones;  // [C][A][2] polarisation-mixing rows (conj J), or nullptr
 };
 
 // Shared memory carve-up (float2 units):
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_fp32(FusedArgs a)
         for (int t = 0; t < a.T; ++t) {
             __syncthreads();
             const uint8_t* fr = a.volt + ((size_t)t * a.C + c) * (size_t)A * P * (a.bits / 4);
-            for (int i = threadIdx.x; i < A * P; i += blockDim.x) vs[i] = load_sample(fr, i, a.bits);
+            stage_frame(vs, fr, A, P, a.bits, a.jones ? a.jones + (size_t)c * A * 2 : nullptr);
             __syncthreads();
             // ---- rows: grid 16-row chunks, FFT along x, keep the slab columns
             for (int r0 = 0; r0 < nyp; r0 += kRowChunk) {
@@ -247,6 +248,7 @@ epic_status fused_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     a.box_y = p->box_max_y;
     a.bits = p->bits;
     a.sub = p->sub;
+    a.jones = p->dt.jones;
     const size_t bytes = sizeof(float2) * fused_smem_elems(a.N, a.A, a.P, a.SW, a.box_x, a.box_y);
     const int items = a.C * a.n_s;
     const int grid = std::min(items, p->sm_count);

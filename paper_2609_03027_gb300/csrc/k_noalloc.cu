@@ -176,8 +176,8 @@ extern "C" epic_status epic_image_static_scratch(epic_plan_t p, const uint8_t* v
     }
     const int C = p->C, P = p->P, N = p->N, A = p->A;
     const size_t per_t = (size_t)C * P * N * N * sizeof(float2);
-    if (p->bits != 4 || p->sub != 0) {
-        p->last_error = "static-scratch imaging: 4+4-bit input and whole-block images only";
+    if (p->bits != 4 || p->sub != 0 || !p->jones.empty()) {
+        p->last_error = "static-scratch imaging: 4+4-bit input, whole-block images, no polarisation mixing only";
         return EPIC_ERR_UNSUPPORTED;
     }
     if (per_t > kStaticScratchBytes) {

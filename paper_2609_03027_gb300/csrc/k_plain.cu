@@ -1,7 +1,8 @@
 // Plain, unfused FP32 path of the EPIC hot loop (paper Sec. 2, Eq. 1-2): the
 // comparator for the fused paths.  Per chunk of time samples, four kernels with
 // HBM round trips between them:
-//   k_plain_grid     unpack 4+4-bit voltages and gather-grid every (t, c, p)
+//   k_plain_grid     unpack the voltages (and mix polarisations, when the plan
+//                    has a mixing kernel) and gather-grid every (t, c, p)
 //                    frame onto a full N x N complex grid (Eq. 1 bracket)
 //   k_plain_fft_rows radix-2 Stockham FFT along x of every grid row (Eq. 1 sum)
 //   k_plain_fft_cols the same along y, on 16-column tiles
@@ -25,12 +26,12 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid(const uint8_t* __restri
                                                          const int* __restrict__ cell_off,
                                                          const int* __restrict__ cell_ptr,
                                                          const int* __restrict__ ce, const float2* __restrict__ cw,
-                                                         float2* __restrict__ grid)
+                                                         const float4* __restrict__ jones, float2* __restrict__ grid)
 {
-    extern __shared__ float2 sv[];  // [A][P] unpacked voltages of this frame
+    extern __shared__ float2 sv[];  // [A][P] unpacked (and pol-mixed) voltages of this frame
     const int tl = blockIdx.x, c = blockIdx.y;
     const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P * (bits / 4);
-    for (int i = threadIdx.x; i < A * P; i += blockDim.x) sv[i] = load_sample(fr, i, bits);
+    stage_frame(sv, fr, A, P, bits, jones ? jones + (size_t)c * A * 2 : nullptr);
     __syncthreads();
     const int4 b = box[c];
     const int* ptr = cell_ptr + cell_off[c];
@@ -63,10 +64,11 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid_g(const uint8_t* __rest
                                                            const int* __restrict__ cell_off,
                                                            const int* __restrict__ cell_ptr,
                                                            const int* __restrict__ ce, const float2* __restrict__ cw,
-                                                           float2* __restrict__ grid)
+                                                           const float4* __restrict__ jones, float2* __restrict__ grid)
 {
     const int tl = blockIdx.x, c = blockIdx.y;
     const uint8_t* fr = volt + ((size_t)(t0 + tl) * C + c) * (size_t)A * P * (bits / 4);
+    const float4* jm = jones ? jones + (size_t)c * A * 2 : nullptr;
     const int4 b = box[c];
     const int* ptr = cell_ptr + cell_off[c];
     const size_t NN = (size_t)N * N;
@@ -81,8 +83,14 @@ __global__ void __launch_bounds__(kThreads) k_plain_grid_g(const uint8_t* __rest
             for (int q = ptr[r]; q < q1; ++q) {
                 const int e = ce[q];
                 const float2 w = cw[q];
-                a0 = cfma(w, load_sample(fr, (size_t)e * P, bits), a0);
-                if (P == 2) a1 = cfma(w, load_sample(fr, (size_t)e * P + 1, bits), a1);
+                if (jm) {
+                    const float4 v = load_pair(fr, e, bits, jm);
+                    a0 = cfma(w, make_float2(v.x, v.y), a0);
+                    a1 = cfma(w, make_float2(v.z, v.w), a1);
+                } else {
+                    a0 = cfma(w, load_sample(fr, (size_t)e * P, bits), a0);
+                    if (P == 2) a1 = cfma(w, load_sample(fr, (size_t)e * P + 1, bits), a1);
+                }
             }
         }
         g[cell] = a0;
@@ -231,10 +239,10 @@ epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
         ev_begin(p, "k_plain_grid", s);
         if ((int)sg <= p->smem_optin)
             k_plain_grid<<<dim3(nt, C), kThreads, sg, s>>>(volt, t0, C, A, P, N, bits, p->dt.box, p->dt.cell_off,
-                                                           p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
+                                                           p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, p->dt.jones, grid);
         else
             k_plain_grid_g<<<dim3(nt, C), kThreads, 0, s>>>(volt, t0, C, A, P, N, bits, p->dt.box, p->dt.cell_off,
-                                                            p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, grid);
+                                                            p->dt.cell_ptr, p->dt.contrib_e, p->dt.contrib_w, p->dt.jones, grid);
         ev_end(p, s);
         const size_t n_rows = (size_t)nt * C * P * N;
         const int rpc = rows_per_cta_for(N);

@@ -26,6 +26,34 @@ __device__ __forceinline__ float2 load_sample(const uint8_t* frame, size_t idx, 
     return unpack44(frame[idx]);
 }
 
+__device__ __forceinline__ float2 cmul(float2 a, float2 b);
+__device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc);
+
+// Both polarisations of element e of a dual-pol frame, as (X re, X im, Y re, Y im).
+// With a polarisation-mixing kernel (Eq. 1 with W_e^{ap}(r) = J_e^{ap} W(r), a
+// complex 2x2 J per element and channel) the sample of output polarisation a is
+// sum_p conj(J_e^{ap}) E_e^p, which is what gridding with W^{ap*} gives once W*
+// is factored out; jm[2 e + a] = (conj J^{a0}, conj J^{a1}).  jm == nullptr: no mixing.
+__device__ __forceinline__ float4 load_pair(const uint8_t* frame, int e, int bits, const float4* jm)
+{
+    const float2 x = load_sample(frame, (size_t)e * 2, bits);
+    const float2 y = load_sample(frame, (size_t)e * 2 + 1, bits);
+    if (!jm) return make_float4(x.x, x.y, y.x, y.y);
+    const float4 r0 = jm[2 * e], r1 = jm[2 * e + 1];
+    const float2 mx = cfma(make_float2(r0.z, r0.w), y, cmul(make_float2(r0.x, r0.y), x));
+    const float2 my = cfma(make_float2(r1.z, r1.w), y, cmul(make_float2(r1.x, r1.y), x));
+    return make_float4(mx.x, mx.y, my.x, my.y);
+}
+
+// Element e of a frame with P = 1 or 2 polarisations as (X re, X im, Y re, Y im),
+// Y zero for one polarisation; mixed by jm as in load_pair (P == 2 only).
+__device__ __forceinline__ float4 load_quad(const uint8_t* frame, int e, int P, int bits, const float4* jm)
+{
+    if (P == 2) return load_pair(frame, e, bits, jm);
+    const float2 x = load_sample(frame, (size_t)e, bits);
+    return make_float4(x.x, x.y, 0.f, 0.f);
+}
+
 // acc + w * v for complex numbers.
 __device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc)
 {
@@ -37,6 +65,22 @@ __device__ __forceinline__ float2 cfma(float2 w, float2 v, float2 acc)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Stage one frame's samples as float2 [A][P] in shared memory (all threads of the
+// block take part), mixed by jm as in load_pair when jm != nullptr (P == 2 only).
+__device__ __forceinline__ void stage_frame(float2* dst, const uint8_t* frame, int A, int P, int bits,
+                                            const float4* jm)
+{
+    if (jm) {
+        for (int e = threadIdx.x; e < A; e += blockDim.x) {
+            const float4 v = load_pair(frame, e, bits, jm);
+            dst[2 * e] = make_float2(v.x, v.y);
+            dst[2 * e + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < A * P; i += blockDim.x) dst[i] = load_sample(frame, i, bits);
+    }
 }
 
 // Radix-2 Stockham autosort FFT with the + sign (Eq. 1), unnormalised, on

@@ -60,7 +60,7 @@ class _PlanDesc(ctypes.Structure):
                 ("n_chan", ctypes.c_int), ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("cell_m", ctypes.POINTER(ctypes.c_double)), ("grid_n", ctypes.c_int), ("gcf", _Gcf),
                 ("path", ctypes.c_int), ("max_time", ctypes.c_int), ("input_bits", ctypes.c_int),
-                ("sub_int", ctypes.c_int)]
+                ("sub_int", ctypes.c_int), ("jones", ctypes.POINTER(ctypes.c_float))]
 
 
 class _TuneReport(ctypes.Structure):
@@ -72,7 +72,8 @@ class _PlanInfo(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("n_prod", ctypes.c_int), ("box_max_x", ctypes.c_int),
                 ("box_max_y", ctypes.c_int), ("time_chunk", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int),
-                ("gemm_flops_per_sample", ctypes.c_double), ("input_bits", ctypes.c_int), ("sub_int", ctypes.c_int)]
+                ("gemm_flops_per_sample", ctypes.c_double), ("input_bits", ctypes.c_int), ("sub_int", ctypes.c_int),
+                ("pol_mix", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -156,7 +157,10 @@ class Plan:
 
     def __init__(self, pos_m, freq_hz, n_pol: int, grid_n: int, gcf_k: int, sigma_cells: float = 1.0,
                  f_ref_hz: Optional[float] = None, freq_scaled: bool = False, cell_m=None, path: str = "auto",
-                 max_time: int = 1024, gcf_table=None, oversample: int = 1, input_bits: int = 4, sub_int: int = 0):
+                 max_time: int = 1024, gcf_table=None, oversample: int = 1, input_bits: int = 4, sub_int: int = 0,
+                 jones=None):
+        """``jones``: optional complex [C][A][2][2] polarisation-mixing matrices J_{c,e}^{ap} (output
+        pol a, input pol p); the element kernel is then W_e^{ap}(r) = J^{ap} W(r) (Eq. 1)."""
         self._lib = load()
         self.pos = np.ascontiguousarray(pos_m, dtype=np.float64).reshape(-1, 2)
         self.freq = np.ascontiguousarray(freq_hz, dtype=np.float64).ravel()
@@ -187,6 +191,13 @@ class Plan:
         d.max_time = self.max_time
         d.input_bits = self.input_bits
         d.sub_int = self.sub_int
+        self.jones = None
+        if jones is not None:
+            j = np.asarray(jones)
+            if j.shape != (self.n_chan, self.n_ant, 2, 2):
+                raise ValueError(f"jones must have shape {(self.n_chan, self.n_ant, 2, 2)}, got {j.shape}")
+            self.jones = np.ascontiguousarray(j, dtype=np.complex64).view(np.float32)
+            d.jones = self.jones.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         h = ctypes.c_void_p()
         _check(self._lib, self._lib.epic_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -195,7 +206,8 @@ class Plan:
     def from_config(cls, cfg, path: str = "auto", max_time: Optional[int] = None) -> "Plan":
         return cls(cfg.pos_m, cfg.freq_hz, cfg.n_pol, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells, cfg.f_ref_hz,
                    cfg.freq_scaled, None, path, cfg.n_time if max_time is None else max_time,
-                   input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0))
+                   input_bits=getattr(cfg, "input_bits", 4), sub_int=getattr(cfg, "sub_int", 0),
+                   jones=getattr(cfg, "jones", None))
 
     def image_shape(self, T: int):
         """Shape of the images of a T-sample block (image sets x C x n_prod x N x N with sub-integrations)."""

@@ -107,3 +107,18 @@ def test_null_plan_calls_are_invalid():
     assert L.epic_image_host(None, None, 0, None, None, 0) == 1
     assert L.epic_sync(None) == 1
     assert L.epic_plan_destroy(None) == 0
+
+
+def test_invalid_polarisation_mixing_rejected_on_host():
+    L = E.load()
+    j = np.zeros((1, 2, 2, 2, 2), dtype=np.float32)
+    j[..., 0, 0, 0] = j[..., 1, 1, 0] = 1.0
+    jp = j.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    d, keep = _desc(n_pol=1, jones=jp)                                    # needs two polarisations
+    assert L.epic_plan_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == 1
+    assert "n_pol" in L.epic_last_error(None).decode()
+    bad = j.copy()
+    bad[0, 1, 0, 1, 1] = np.nan
+    d, keep = _desc(jones=bad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    assert L.epic_plan_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == 1
+    assert "finite" in L.epic_last_error(None).decode()

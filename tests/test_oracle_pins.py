@@ -364,3 +364,69 @@ def test_one_frame_transient_found_in_its_sub_integration():
     t_pix = (N // 2 + 2, N // 2 - 8)                             # (iy, ix) of (l, m) = (-0.5, 0.125)
     assert np.unravel_index(np.argmax(sub[1]), sub[1].shape) == t_pix
     assert sub[1][t_pix] > 5 * max(sub[0][t_pix], sub[2][t_pix])
+
+
+# ----------------------------------------------------------------------------- polarisation mixing
+
+def _mix_cfg(seed, **kw):
+    base = dict(n_ant=14, n_chan=2, n_pol=2, grid_n=16, gcf_k=3, n_time=6, seed=seed, diameter_m=5.0)
+    base.update(kw)
+    return synth.small_config(**base)
+
+
+def test_identity_and_swap_kernels_reproduce_the_unmixed_products():
+    # W^{ap} = delta_ap W is the unmixed path exactly; J = [[0, 1], [1, 0]] exchanges the
+    # polarisations: XX <-> YY, XY -> conj(XY)
+    cfg = _mix_cfg(61)
+    v = synth.make_voltages(cfg)
+    base = oracle.image_cfg(cfg, v)
+    eye = np.broadcast_to(np.eye(2, dtype=np.complex128), (cfg.n_chan, cfg.n_ant, 2, 2))
+    assert np.array_equal(oracle.image_cfg(dataclasses.replace(cfg, jones=eye), v), base)
+    swap = np.broadcast_to(np.array([[0, 1], [1, 0]], dtype=np.complex128), eye.shape)
+    sw = oracle.image_cfg(dataclasses.replace(cfg, jones=swap), v)
+    assert np.array_equal(sw[:, 0], base[:, 1]) and np.array_equal(sw[:, 1], base[:, 0])
+    assert np.array_equal(sw[:, 2], base[:, 2]) and np.array_equal(sw[:, 3], -base[:, 3])
+
+
+def test_channel_wide_kernel_mixes_the_image_products_linearly():
+    # one J for every element of a channel: gridding and the transform are linear, so
+    # E'^a = sum_p conj(J^{ap}) E^p per pixel and I'^{ab} = sum_{p,q} conj(J^{ap}) J^{bq} I^{pq}
+    # with I^{YX} = conj(I^{XY}); a non-symmetric complex J catches a transposed or
+    # unconjugated kernel
+    cfg = _mix_cfg(62)
+    v = synth.make_voltages(cfg)
+    base = oracle.image_cfg(cfg, v)
+    Jc = np.array([[[0.9 + 0.3j, 0.2 - 0.1j], [-0.15 + 0.25j, 1.1 - 0.4j]],
+                   [[0.7 - 0.2j, -0.3 + 0.05j], [0.1 + 0.2j, 0.8 + 0.6j]]])
+    J = np.repeat(Jc[:, None], cfg.n_ant, axis=1)
+    got = oracle.image_cfg(dataclasses.replace(cfg, jones=J), v)
+    for c in range(cfg.n_chan):
+        xy = base[c, 2] + 1j * base[c, 3]
+        Ipq = np.array([[base[c, 0], xy], [np.conj(xy), base[c, 1]]])     # [p][q][N][N]
+        M = np.einsum("ap,bq,pqyx->abyx", np.conj(Jc[c]), Jc[c], Ipq)
+        peak = np.abs(M[0, 0]).max() + np.abs(M[1, 1]).max()
+        assert np.abs(got[c, 0] - M[0, 0].real).max() <= 1e-12 * peak
+        assert np.abs(got[c, 1] - M[1, 1].real).max() <= 1e-12 * peak
+        assert np.abs(got[c, 2] + 1j * got[c, 3] - M[0, 1]).max() <= 1e-12 * peak
+        assert np.abs(M[0, 0].imag).max() <= 1e-12 * peak
+
+
+def test_per_element_kernels_match_the_correlator_route():
+    # a different random J per element and channel (8+8-bit input): the oracle's double sum
+    # of Eq. 1 against pairwise visibilities of the mixed voltages (no gridding, no FFT shared)
+    cfg = dataclasses.replace(_mix_cfg(63, n_ant=10), input_bits=8)
+    J = synth.make_jones(cfg, seed=3, gain_rms=0.2, leak_rms=0.3)
+    v8 = synth.make_voltages(cfg)
+    got = oracle.image_cfg(dataclasses.replace(cfg, jones=J), v8)
+    ref = bruteforce.image(v8, cfg.pos_m, cfg.freq_hz, 2, cfg.grid_n, cfg.gcf_k, cfg.sigma_cells, cfg.f_ref_hz,
+                           cfg.freq_scaled, jones=J, input_bits=8)
+    peak = np.abs(ref[:, :2]).max()
+    assert np.abs(got - ref).max() <= 1e-9 * peak
+
+
+def test_mixing_kernel_rejected_for_one_polarisation():
+    cfg = _mix_cfg(64, n_pol=1)
+    v = synth.make_voltages(cfg)
+    J = np.ones((cfg.n_chan, cfg.n_ant, 2, 2), dtype=np.complex128)
+    with pytest.raises(oracle.OracleError):
+        oracle.image_cfg(dataclasses.replace(cfg, jones=J), v)

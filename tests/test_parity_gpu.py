@@ -230,3 +230,32 @@ def test_eight_bit_input_and_sub_integrations(path, bits, sub):
             assert_parity(got, ref, path, f"bits={bits}")
         host = plan.image_host(v)
         assert np.array_equal(host, got)
+
+
+@pytest.mark.parametrize("path", GPU_PATHS)
+@pytest.mark.parametrize("bits,sub", [(4, 0), (8, 3)])
+def test_polarisation_mixing_kernels(path, bits, sub):
+    # per-element, per-channel 2x2 mixing kernels J W (Eq. 1's W_e^{ap}); then the exchange
+    # kernel [[0, 1], [1, 0]] must permute the unmixed products exactly (XX <-> YY, XY -> conj)
+    cfg = dataclasses.replace(synth.small_config(n_ant=40, n_chan=3, n_pol=2, grid_n=32, gcf_k=3, n_time=12,
+                                                 seed=71 + bits, diameter_m=9.0, sigma=0.7),
+                              input_bits=bits, sub_int=sub)
+    J = synth.make_jones(cfg, seed=5, gain_rms=0.2, leak_rms=0.2)
+    mixed = dataclasses.replace(cfg, jones=J)
+    v = synth.make_voltages(cfg)
+    ref = oracle_image(mixed, v)
+    got = run_gpu(mixed, v, path)
+    assert got.shape == ref.shape
+    for k in range(ref.shape[0] if sub else 1):
+        assert_parity(got[k] if sub else got, ref[k] if sub else ref, path, f"mixed, set {k}")
+    swap = np.broadcast_to(np.array([[0, 1], [1, 0]], dtype=np.complex128), J.shape)
+    base = run_gpu(cfg, v, path)
+    sw = run_gpu(dataclasses.replace(cfg, jones=swap), v, path)
+    assert np.array_equal(sw[..., 0, :, :], base[..., 1, :, :])
+    assert np.array_equal(sw[..., 1, :, :], base[..., 0, :, :])
+    assert np.array_equal(sw[..., 2, :, :], base[..., 2, :, :])
+    # Im XY = Im X conj(Y) accumulates with fused multiply-adds whose rounding is not odd under
+    # the exchange: equal to FP32 rounding
+    assert np.abs(sw[..., 3, :, :] + base[..., 3, :, :]).max() <= 1e-6 * np.abs(base[..., :2, :, :]).max()
+    with E.Plan.from_config(mixed, path=path) as plan:
+        assert plan.info()["pol_mix"] == 1
