@@ -60,6 +60,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         : "memory");
 }
 
+// Bulk prefetch of global memory into L2 (TMA engine, 1-D): no completion to wait for.
+// 16-byte aligned address, size a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src_gmem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
+}
+
 // Bulk copy shared -> global (TMA engine, 1-D), tracked by bulk groups of the
 // issuing thread: commit after the copies of a group, then wait until at most
 // `n` groups still read their shared-memory source.
