@@ -194,8 +194,7 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  *   FUSED_FP32    slab         image columns per work item
  *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
  *                              control warp does, 3: a control warpgroup with its own
- *                              register budget does, 4: as 3 on 32-column work items with
- *                              two stage-2 buffers (when the occupied box allows each);
+ *                              register budget does (when the occupied box allows each);
  *                 split        work of the control-warp kernel: -1 automatic, 0 whole work
  *                              items per SM, 1 equal (item, time sample) shares per SM;
  *                 grid_kernel  gridding kernel: 1 row-major cell walk, 2 cells in lists sorted

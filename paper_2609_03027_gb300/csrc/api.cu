@@ -57,8 +57,6 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.a2w_off);
     cudaFree(p->tc.a1p);
     cudaFree(p->tc.a1p_off);
-    cudaFree(p->tc.a1d);
-    cudaFree(p->tc.a1d_off);
     cudaFree(p->tc.gtask);
     cudaFree(p->tc.partial);
     cudaFree(p->tc.counters);

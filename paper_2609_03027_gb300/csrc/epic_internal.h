@@ -73,13 +73,7 @@ struct TcState {
     int n_gp = 0;                  // 64-column pairs per channel
     float* partial = nullptr;      // k_dftgemm_ws3: partial sums of items split between blocks
     int* counters = nullptr;       // k_dftgemm_ws3: per item, parts stored so far
-    int split = -1;                // k_dftgemm_ws3/ws4 work split: -1 auto, 0 whole items, 1 equal shares
-    bool ws4 = false;              // 32-kx kernel with two stage-2 buffers (k_dftgemm_ws4) fits
-    unsigned ws4_sB1 = 0, ws4_sB2 = 0, ws4_b2_bytes = 0;
-    int ws4_smem = 0;
-    uint16_t* a1d = nullptr;       // stage-1 operands per (channel, 32-column kx group), rows twice
-    long long* a1d_off = nullptr;
-    int n_g32 = 0;                 // 32-column kx groups per channel
+    int split = -1;                // k_dftgemm_ws3 work split: -1 auto, 0 whole items, 1 equal shares
 };
 
 struct KernelEvent {

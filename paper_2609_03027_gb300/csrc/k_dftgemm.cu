@@ -1791,13 +1791,14 @@ __global__ void __launch_bounds__(kWs2Threads, 1) k_dftgemm_ws2(MmaArgs a)
 
 // ---------------------------------------------------------------------------------
 // Third warp-specialised kernel: 16 epilogue warps and a control warpgroup in
-// separate register budgets (setmaxnreg), so one thread can issue every MMA and
-// tile copy of a frame -- blocking while the tensor pipe is busy -- without holding
-// up any epilogue warp.  Work item, operands and TMEM layout as k_dftgemm_ws2:
-//   control (warp 16, lane 0), per frame t:
-//     wait d1_full(t) -> copy tile t+2 into the buffer S1(t) read;
-//     wait b2_full(t) [and d2_empty(t-1)] -> S2(t) -> d2_full;
-//     wait tile t+2 -> S1(t+2) -> d1_full[t&1]
+// separate register budgets (setmaxnreg), so that the threads issuing the MMAs and
+// tile copies -- blocking while the tensor pipe is busy -- hold up no epilogue warp.
+// Work item, operands and TMEM layout as k_dftgemm_ws2:
+//   stage-1 issuer (warp 17, lane 0), per frame t:
+//     wait d1_full(t) -> copy tile t+2 into the buffer S1(t) read (tile t+10 -> L2);
+//     wait b2_full(t) and tile t+2 -> S1(t+2) -> d1_full[t&1]
+//   stage-2 issuer (warp 16, lane 0), per frame t:
+//     wait b2_full(t) [and d2_empty(t-1)] -> S2(t) -> d2_full
 //   epilogue warps 0-15, per frame t:
 //     wait d1_full(t) -> epilogue 1 (t) -> arrive b2_full[t&1];
 //     wait d2_full(t-1) -> epilogue 2 (t-1) -> arrive d2_empty
@@ -1915,7 +1916,8 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         // ------------------------------------------------------------ control warpgroup
         asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
         uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
-        const bool boss = warp == 16 && lane == 0;
+        const bool iss1 = warp == 17 && lane == 0;  // stage 1: A1, grid tiles, S1 chains
+        const bool iss2 = warp == 16 && lane == 0;  // stage 2 chains
         long long w = wb0;
         for (int it = 0;; ++it) {
             int item, fs, nt;  // work item, its first frame and the frames of this segment
@@ -1939,7 +1941,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
             const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
             const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride + (size_t)fs * frame_step;
-            if (boss) {
+            if (iss1) {
                 const uint32_t a1_bytes = 256u * pad64(K1);
                 tc::mbar_expect_tx(&bar_a, a1_bytes);
                 tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
@@ -1952,13 +1954,13 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                     tc::bulk_prefetch_l2(tiles_c + (size_t)j * frame_step, tile_bytes);
             }
             bar_all(1);  // A2 is in TMEM
-            if (boss) {
-                const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, 128 * P);
-                auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
-                    const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
-                    ph ^= 1u << slot;
-                    return r;
-                };
+            auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
+                const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
+                ph ^= 1u << slot;
+                return r;
+            };
+            if (iss1) {  // per frame t: S1(t) done -> tile t+2 into its buffer; E1(t) done -> S1(t+2)
+                const uint32_t id1 = tc::idesc_f16_f32(128, N1);
                 auto issue_s1 = [&](int t) {
                     issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
                              tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
@@ -1975,14 +1977,28 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 for (int t = 0; t < nt && good; ++t) {
                     const int sl = t & 1;
                     good = wait_bit(&d1_full[sl], ph_d1, sl);  // S1(t) done: its tile buffer is free
-                    if (!good) break;
-                    if (t + 2 < nt) {
+                    if (good && t + 2 < nt) {
                         tc::mbar_expect_tx(&tile_full[sl], tile_bytes);
                         tc::bulk_g2s(sbase + a.sB1 + (size_t)sl * a.b1_bytes, tiles_c + (size_t)(t + 2) * frame_step,
                                      tile_bytes, &tile_full[sl]);
                     }
-                    if (t + 2 + kTilePrefetch < nt)
+                    if (good && t + 2 + kTilePrefetch < nt)
                         tc::bulk_prefetch_l2(tiles_c + (size_t)(t + 2 + kTilePrefetch) * frame_step, tile_bytes);
+                    if (good) good = wait_bit(&b2_full[sl], ph_b2, sl);  // E1(t) has read D1[sl]
+                    if (good && t + 2 < nt) {
+                        good = wait_bit(&tile_full[sl], ph_tile, sl);
+                        if (good) {
+                            tc::fence_after_sync();
+                            issue_s1(t + 2);
+                        }
+                    }
+                }
+                if (!good) err_sh = 1;
+            } else if (iss2) {  // per frame t: E1(t) wrote B2[t&1] and E2(t-1) read D2 -> S2(t)
+                const uint32_t id2 = tc::idesc_f16_f32(128, 128 * P);
+                bool good = true;
+                for (int t = 0; t < nt && good; ++t) {
+                    const int sl = t & 1;
                     good = wait_bit(&b2_full[sl], ph_b2, sl);
                     if (good && t >= 1) good = wait_bit(&d2_empty, ph_e2, 0);
                     if (!good) break;
@@ -1990,12 +2006,6 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                     issue_ts(K2 / 16, tmem + 256, tmem + a2col, tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes),
                              R2 * 128, id2);
                     tc::mma_commit(&d2_full);
-                    if (t + 2 < nt) {
-                        good = wait_bit(&tile_full[sl], ph_tile, sl);
-                        if (!good) break;
-                        tc::fence_after_sync();
-                        issue_s1(t + 2);
-                    }
                 }
                 if (!good) err_sh = 1;
             }
@@ -2159,406 +2169,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 
 
 
-// ---------------------------------------------------------------------------------
-// Fourth warp-specialised kernel: work items of 32 kx -- (channel, 128-row ky block,
-// 32-column kx group) -- so that the stage-2 result (N = 64 P columns) fits in TMEM
-// twice: the tensor core computes frame t+1 into one D2 buffer while the epilogue
-// warps read frame t from the other, and each epilogue thread owns 8 pixels (32
-// accumulators) whose frame values arrive in a single round of TMEM loads.  Stage 1
-// keeps M = 128: A1 rows 0..63 hold the real DFT rows of the group's 32 kx twice,
-// rows 64..127 the imaginary rows twice, so every lane quarter of D1 holds Hr or Hi
-// of the group and all 16 warps share epilogue 1.
-//   control (warp 16, lane 0), per frame t (slot s = t & 1):
-//     wait d1_full[s](t) -> copy tile t+2 into the buffer S1(t) read;
-//     wait b2_full[s](t) [and d2_empty[s](t-2)] -> S2(t) into D2[s] -> d2_full[s];
-//     wait tile t+2 -> S1(t+2) -> d1_full[s]
-//   epilogue warps 0-15, per frame t:
-//     wait d1_full[s](t) -> epilogue 1 (t) into B2[s] -> arrive b2_full[s];
-//     wait d2_full[s^1](t-1) -> epilogue 2 (t-1) -> arrive d2_empty[s^1] when S2(t+1) will reuse it
-// TMEM: D1[0..1] at 0 and d1_cols, A2 at 2 d1_cols, D2[b] at 256 + 64 P b.
-// Items are separated by two block-wide named barriers (operands loaded; item done).
-constexpr int kWs4Threads = 640;
 
-// Epilogue 2 of k_dftgemm_ws4: 8 kx x (X, Y) of the warp's 32 ky rows, one TMEM round.
-__device__ __forceinline__ void ws4_epilogue2(uint32_t taddr, int P, float (&axx)[8], float (&ayy)[8],
-                                              float (&arx)[8], float (&aix)[8])
-{
-    uint32_t xr[8], xi[8], yr[8], yi[8];
-    tmem_ld8(taddr, xr);
-    tmem_ld8(taddr + 32, xi);
-    if (P == 2) {
-        tmem_ld8(taddr + 64, yr);
-        tmem_ld8(taddr + 96, yi);
-    }
-    tc::tmem_wait_ld(xr);
-    tc::tmem_wait_ld(xi);
-    if (P == 2) {
-        tc::tmem_wait_ld(yr);
-        tc::tmem_wait_ld(yi);
-    }
-    products<8>(xr, xi, yr, yi, P, 0, axx, ayy, arx, aix);
-}
-
-// The 8 pixels a k_dftgemm_ws4 epilogue thread owns in one product image: row ky,
-// kx = kx0 .. kx0 + 7; written, or added to what is there.
-__device__ __forceinline__ void ws4_store_own(float* img, int N, int ky, int kx0, int accumulate, const float (&v)[8])
-{
-    if (ky >= N || kx0 >= N) return;
-    float* op = img + (size_t)ky * N + kx0;
-    if (kx0 + 8 <= N) {
-#pragma unroll
-        for (int i = 0; i < 8; i += 4) {
-            float4 w = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            if (accumulate) {
-                const float4 u = *reinterpret_cast<const float4*>(op + i);
-                w.x += u.x;
-                w.y += u.y;
-                w.z += u.z;
-                w.w += u.w;
-            }
-            *reinterpret_cast<float4*>(op + i) = w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (kx0 + i < N) op[i] = (accumulate ? op[i] : 0.f) + v[i];
-    }
-}
-
-// A split work item of k_dftgemm_ws4 (equal shares) after this block stored its part:
-// as ws3_split_finish, with parts of 4 x 4096 values (8 per thread).
-__device__ __noinline__ void ws4_split_finish(const MmaArgs& a, int item, int c, int ky, int kx0, size_t px,
-                                              long long U, int tid, int* split_slot, int* split_n)
-{
-    __threadfence();
-    asm volatile("bar.sync 3, 512;" ::: "memory");
-    if (tid == 0) {
-        const long long s0 = (long long)item * a.nt, s1 = s0 + a.nt - 1;
-        const long long G = gridDim.x;
-        auto owner = [&](long long f) {  // block whose range [U b / G, U (b + 1) / G) holds f
-            long long b = f * G / U;
-            while (b + 1 < G && U * (b + 1) / G <= f) ++b;
-            while (b > 0 && U * b / G > f) --b;
-            return (int)b;
-        };
-        int n = 0;
-        const int b1 = owner(s1);
-        for (int b = owner(s0); b <= b1; ++b) {
-            const long long bw0 = U * b / G;
-            if (bw0 == U * (b + 1) / G) continue;  // no frames: no part
-            split_slot[n++] = 2 * b + (s0 <= bw0 ? 0 : 1);
-        }
-        const bool last = atomicAdd(&a.counters[item], 1) == n - 1;
-        if (last) a.counters[item] = 0;  // ready for the next launch
-        *split_n = last ? n : 0;
-    }
-    asm volatile("bar.sync 3, 512;" ::: "memory");
-    const int n = *split_n;
-    if (n > 0 && ky < a.N && kx0 < a.N) {
-        __threadfence();
-        const size_t NN = (size_t)a.N * a.N;
-        for (int pr = 0; pr < a.nprod; ++pr) {
-            float sum[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sum[i] = 0.f;
-            for (int k = 0; k < n; ++k) {
-                const float* q = a.partial + ((size_t)split_slot[k] * 4 + pr) * 4096 + px;
-#pragma unroll
-                for (int i = 0; i < 8; i += 4) {
-                    const float4 u = __ldcg(reinterpret_cast<const float4*>(q + i));
-                    sum[i] += u.x;
-                    sum[i + 1] += u.y;
-                    sum[i + 2] += u.z;
-                    sum[i + 3] += u.w;
-                }
-            }
-            ws4_store_own(a.out + ((size_t)c * a.nprod + pr) * NN, a.N, ky, kx0, a.accumulate, sum);
-        }
-    }
-}
-
-__device__ __forceinline__ void bar_all4(int id)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWs4Threads) : "memory");
-}
-
-template <int MODE>  // 0: whole items, 1: equal shares (split items), 2: whole items, sub-integrations
-__global__ void __launch_bounds__(kWs4Threads, 1) k_dftgemm_ws4(MmaArgs a)
-{
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bar_a, d1_full[2], b2_full[2], d2_full[2], d2_empty[2], tile_full[2];
-    __shared__ uint32_t tmem_sh;
-    __shared__ int err_sh;
-    __shared__ int split_slot[kWs3MaxBlocks];  // partial slots of a split item, in block order
-    __shared__ int split_n;                    // > 0: this block completes the item; sum split_n slots
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        tc::tmem_alloc(&tmem_sh, 512);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        tc::mbar_init(&bar_a, 1);
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&d1_full[i], 1);
-            tc::mbar_init(&b2_full[i], 16);
-            tc::mbar_init(&tile_full[i], 1);
-            tc::mbar_init(&d2_full[i], 1);
-            tc::mbar_init(&d2_empty[i], 16);
-        }
-        err_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = tmem_sh;
-    uint8_t* sbase = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
-    uint8_t* sA1 = sbase + a.sA1;
-    const int P = a.P;
-    const int R2 = 64 * P;  // B2 rows: [Hr | -Hi] and [Hi | Hr] of 32 kx per pol
-    const uint32_t a2col = 2u * a.d1_cols;
-    const int items = a.n_ch * a.n_kb * a.n_g;
-    const long long U = (long long)items * a.nt;
-    const long long wb0 = U * blockIdx.x / gridDim.x, wb1 = U * (blockIdx.x + 1) / gridDim.x;
-
-    if (warp >= 16) {
-        // ------------------------------------------------------------ control warpgroup
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
-        uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
-        const bool boss = warp == 16 && lane == 0;
-        long long w = wb0;
-        for (int it = 0;; ++it) {
-            int item, fs, nt;  // work item, its first frame and the frames of this segment
-            if (MODE == 1) {
-                if (w >= wb1) break;
-                item = (int)(w / a.nt);
-                fs = (int)(w % a.nt);
-                nt = (int)min((long long)(a.nt - fs), wb1 - w);
-                w += nt;
-            } else {
-                item = blockIdx.x + it * gridDim.x;
-                if (item >= items) break;
-                fs = 0;
-                nt = a.nt;
-            }
-            const int g = item % a.n_g, cl = item / (a.n_g * a.n_kb);
-            const int c = a.c0 + cl;
-            const int4 bx = a.box[c];
-            const int nxp = bx.z, nyp = bx.w;
-            const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
-            const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
-            const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
-            const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride + (size_t)fs * frame_step;
-            if (boss) {
-                const uint32_t a1_bytes = 256u * pad64(K1);
-                tc::mbar_expect_tx(&bar_a, a1_bytes);
-                tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
-                for (int j = 0; j < 2 && j < nt; ++j) {
-                    tc::mbar_expect_tx(&tile_full[j], tile_bytes);
-                    tc::bulk_g2s(sbase + a.sB1 + (size_t)j * a.b1_bytes, tiles_c + (size_t)j * frame_step, tile_bytes,
-                                 &tile_full[j]);
-                }
-                for (int j = 2; j < 2 + kTilePrefetch && j < nt; ++j)  // later tiles: HBM -> L2 ahead of use
-                    tc::bulk_prefetch_l2(tiles_c + (size_t)j * frame_step, tile_bytes);
-            }
-            bar_all4(1);  // A2 is in TMEM
-            if (boss) {
-                const uint32_t id1 = tc::idesc_f16_f32(128, N1), id2 = tc::idesc_f16_f32(128, R2);
-                auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
-                    const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
-                    ph ^= 1u << slot;
-                    return r;
-                };
-                auto issue_s1 = [&](int t) {
-                    issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
-                             tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
-                    tc::mma_commit(&d1_full[t & 1]);
-                };
-                bool good = wait_bit(&bar_a, ph_a, 0);
-                for (int j = 0; j < 2 && j < nt && good; ++j) {
-                    good = wait_bit(&tile_full[j], ph_tile, j);
-                    if (good) {
-                        tc::fence_after_sync();
-                        issue_s1(j);
-                    }
-                }
-                for (int t = 0; t < nt && good; ++t) {
-                    const int sl = t & 1;
-                    good = wait_bit(&d1_full[sl], ph_d1, sl);  // S1(t) done: its tile buffer is free
-                    if (!good) break;
-                    if (t + 2 < nt) {
-                        tc::mbar_expect_tx(&tile_full[sl], tile_bytes);
-                        tc::bulk_g2s(sbase + a.sB1 + (size_t)sl * a.b1_bytes, tiles_c + (size_t)(t + 2) * frame_step,
-                                     tile_bytes, &tile_full[sl]);
-                    }
-                    if (t + 2 + kTilePrefetch < nt)
-                        tc::bulk_prefetch_l2(tiles_c + (size_t)(t + 2 + kTilePrefetch) * frame_step, tile_bytes);
-                    good = wait_bit(&b2_full[sl], ph_b2, sl);
-                    if (good && t >= 2) good = wait_bit(&d2_empty[sl], ph_e2, sl);  // E2(t-2) read D2[sl]
-                    if (!good) break;
-                    tc::fence_after_sync();
-                    issue_ts(K2 / 16, tmem + 256 + R2 * sl, tmem + a2col,
-                             tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes), R2 * 128, id2);
-                    tc::mma_commit(&d2_full[sl]);
-                    if (t + 2 < nt) {
-                        good = wait_bit(&tile_full[sl], ph_tile, sl);
-                        if (!good) break;
-                        tc::fence_after_sync();
-                        issue_s1(t + 2);
-                    }
-                }
-                if (!good) err_sh = 1;
-            }
-            __syncwarp();
-            bar_all4(2);  // item done
-            if (err_sh) break;
-        }
-    } else {
-        // ------------------------------------------------------------ epilogue warps
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 104;" ::: "memory");
-        uint32_t ph_d1 = 0, ph_d2 = 0;
-        const int q4 = warp & 3, j4 = warp >> 2;
-        const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
-        const bool imw = (q4 >> 1) != 0;  // lane quarters 2, 3: Hi; 0, 1: Hr (each twice)
-        const int dup = q4 & 1;
-        long long w = wb0;
-        for (int it = 0;; ++it) {
-            int item, fs, nt;
-            if (MODE == 1) {
-                if (w >= wb1) break;
-                item = (int)(w / a.nt);
-                fs = (int)(w % a.nt);
-                nt = (int)min((long long)(a.nt - fs), wb1 - w);
-                w += nt;
-            } else {
-                item = blockIdx.x + it * gridDim.x;
-                if (item >= items) break;
-                fs = 0;
-                nt = a.nt;
-            }
-            const bool first_seg = it == 0;
-            const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
-            const int c = a.c0 + cl;
-            const int4 bx = a.box[c];
-            const int nyp = bx.w;
-            const int K2 = 2 * nyp;
-            if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
-                const uint32_t* src =
-                    a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
-                for (int jj = 0; jj < K2 / 2; jj += 8) {
-                    uint32_t r[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
-                    tc::tmem_st8(tmem + lane_base + a2col + jj, r);
-                }
-                tc::tmem_wait_st();
-            }
-            tc::fence_before_sync();
-            bar_all4(1);
-            tc::fence_after_sync();
-            float axx[8], ayy[8], arx[8], aix[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
-            // epilogue 1 share: pol p1, y chunks [yc0, yc1) of the part (Hr / Hi) this quarter holds
-            const int nyc = nyp >> 3;
-            int p1, pi, np;
-            if (P == 2) {
-                p1 = j4 >> 1;
-                pi = 2 * dup + (j4 & 1);
-                np = 4;
-            } else {
-                p1 = 0;
-                pi = 4 * dup + j4;
-                np = 8;
-            }
-            const int yc0 = (nyc * pi) / np, yc1 = (nyc * (pi + 1)) / np;
-            // pixels: row ky = 128 kb + 32 q4 + lane, kx = 32 g + 8 j4 .. + 7
-            const int ky = 128 * kb + 32 * q4 + lane;
-            const int kx0 = 32 * g + 8 * j4;
-            const uint32_t e2addr = tmem + lane_base + 256 + 8 * j4;
-            auto flush_interval = [&](int f) {
-                const size_t NN = (size_t)a.N * a.N;
-                float* o = a.out + ((size_t)(a.iv0 + f / a.sub) * a.C + c) * a.nprod * NN;
-                ws4_store_own(o, a.N, ky, kx0, a.accumulate, axx);
-                if (a.nprod == 4) {
-                    ws4_store_own(o + NN, a.N, ky, kx0, a.accumulate, ayy);
-                    ws4_store_own(o + 2 * NN, a.N, ky, kx0, a.accumulate, arx);
-                    ws4_store_own(o + 3 * NN, a.N, ky, kx0, a.accumulate, aix);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
-            };
-            bool live = true;
-            for (int t = 0; t < nt && live; ++t) {
-                const int sl = t & 1;
-                const bool w1 = tc::mbar_wait(&d1_full[sl], (ph_d1 >> sl) & 1u, kWaitBudget);
-                ph_d1 ^= 1u << sl;
-                __syncwarp();
-                tc::fence_after_sync();
-                if (w1)
-                    ws2_epilogue1<2>(tmem + lane_base + sl * a.d1_cols + p1 * nyp, nyp, yc0, yc1, imw, lane,
-                                     sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * p1, R2);
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&b2_full[sl]);
-                bool w2 = true;
-                if (t >= 1) {
-                    const int so = sl ^ 1;  // D2 buffer of frame t-1
-                    w2 = tc::mbar_wait(&d2_full[so], (ph_d2 >> so) & 1u, kWaitBudget);
-                    ph_d2 ^= 1u << so;
-                    __syncwarp();
-                    tc::fence_after_sync();
-                    if (w2) ws4_epilogue2(e2addr + R2 * so, P, axx, ayy, arx, aix);
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0 && t + 1 < nt) mbar_arrive(&d2_empty[so]);  // S2(t+1) reuses D2[so]
-                    if (MODE == 2 && w2 && t % a.sub == 0) flush_interval(t - 1);  // frame t-1 ends one
-                }
-                if (!w1 || !w2) err_sh = 1;
-                live = !__any_sync(0xffffffffu, err_sh != 0);
-            }
-            if (nt > 0 && live) {
-                const int so = (nt - 1) & 1;
-                const bool w2 = tc::mbar_wait(&d2_full[so], (ph_d2 >> so) & 1u, kWaitBudget);
-                ph_d2 ^= 1u << so;
-                if (!w2) err_sh = 1;
-                __syncwarp();
-                tc::fence_after_sync();
-                if (w2) ws4_epilogue2(e2addr + R2 * so, P, axx, ayy, arx, aix);
-                if (MODE == 2 && w2) flush_interval(nt - 1);
-            }
-            tc::fence_before_sync();
-            bar_all4(2);
-            tc::fence_after_sync();
-            if (err_sh) break;
-            if (MODE == 1 && (fs != 0 || nt != a.nt)) {
-                const size_t px = (size_t)(32 * q4 + lane) * 32 + 8 * j4;
-                float* o = a.partial + (2 * (size_t)blockIdx.x + (first_seg ? 0 : 1)) * 4 * 4096 + px;
-                ws4_store_own(o, 1 << 30, 0, 0, 0, axx);
-                if (a.nprod == 4) {
-                    ws4_store_own(o + 4096, 1 << 30, 0, 0, 0, ayy);
-                    ws4_store_own(o + 2 * 4096, 1 << 30, 0, 0, 0, arx);
-                    ws4_store_own(o + 3 * 4096, 1 << 30, 0, 0, 0, aix);
-                }
-                ws4_split_finish(a, item, c, ky, kx0, px, U, tid, split_slot, &split_n);
-            } else if (MODE != 2) {
-                const size_t NN = (size_t)a.N * a.N;
-                float* o = a.out + (size_t)c * a.nprod * NN;
-                ws4_store_own(o, a.N, ky, kx0, a.accumulate, axx);
-                if (a.nprod == 4) {
-                    ws4_store_own(o + NN, a.N, ky, kx0, a.accumulate, ayy);
-                    ws4_store_own(o + 2 * NN, a.N, ky, kx0, a.accumulate, arx);
-                    ws4_store_own(o + 3 * NN, a.N, ky, kx0, a.accumulate, aix);
-                }
-            }
-        }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
-    if (err_sh && tid == 0) atomicExch(a.status, 1);
-}
 
 }  // namespace
 
@@ -2566,8 +2177,8 @@ __global__ void __launch_bounds__(kWs4Threads, 1) k_dftgemm_ws4(MmaArgs a)
 // chunk) take at most `budget` bytes, and the tile buffer for them.
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 {
-    if (variant < 1 || variant > 4 || (variant == 4 ? !p->tc.ws4 : !p->tc.ws) ||
-        (p->sub > 0 && variant != 3 && variant != 4) || (variant >= 3 && p->sm_count > kWs3MaxBlocks))
+    if (variant < 1 || variant > 3 || !p->tc.ws || (p->sub > 0 && variant != 3) ||
+        (variant == 3 && p->sm_count > kWs3MaxBlocks))
         return EPIC_ERR_UNSUPPORTED;
     p->tc.ws_variant = variant;
     return EPIC_OK;
@@ -2577,7 +2188,7 @@ epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 // items than SMs), 0 = whole items per block, 1 = equal (item, frame) shares.
 epic_status dftgemm_set_split(epic_plan_s* p, int mode)
 {
-    if (!(p->tc.ws || p->tc.ws4) || mode < -1 || mode > 1 || (p->sub > 0 && mode == 1)) return EPIC_ERR_UNSUPPORTED;
+    if (!p->tc.ws || mode < -1 || mode > 1 || (p->sub > 0 && mode == 1)) return EPIC_ERR_UNSUPPORTED;
     p->tc.split = mode;
     return EPIC_OK;
 }
@@ -2719,21 +2330,6 @@ epic_status dftgemm_setup(epic_plan_s* p)
             p->tc.smem = (int)(need_ws + 1024);
         }
     }
-    // 32-kx variant (k_dftgemm_ws4): A1 + 2 tiles + 2 single-width B2 buffers; two D2 buffers in TMEM
-    {
-        const int tm = 2 * N1max + p->box_max_y;
-        const size_t b2q = align_up(2ull * 64 * P * K2max, 1024);
-        const size_t sb1 = align_up(256ull * K1max, 1024);
-        const size_t need4 = sb1 + 2 * b1 + 2 * b2q;
-        p->tc.ws4 = tm <= 256 && need4 <= limit;
-        if (p->tc.ws4) {
-            p->tc.ws4_sB1 = (unsigned)sb1;
-            p->tc.ws4_sB2 = (unsigned)(sb1 + 2 * b1);
-            p->tc.ws4_b2_bytes = (unsigned)b2q;
-            p->tc.ws4_smem = (int)(need4 + 1024);
-            p->tc.d1_cols = N1max;
-        }
-    }
     // fast variant: 2 D1 slots + A2 (FP16 pairs) in TMEM columns [0, 256); 3 tiles + 2 B2 in shared memory
     {
         const int tm = 2 * N1max + p->box_max_y;  // 2 N1 + K2/2 columns
@@ -2859,36 +2455,6 @@ epic_status dftgemm_setup(epic_plan_s* p)
         }
     }
     p->tc.n_gp = n_gp;
-    // A1 per (channel, 32-column group s) for k_dftgemm_ws4: rows 0..63 re, 64..127 im of
-    // kx = 32 s + j, each set twice (rows j and 32 + j)
-    const int n_g32 = (N + 31) / 32;
-    std::vector<long long> a1d_off((size_t)C * n_g32);
-    size_t n1d = 0;
-    for (int c = 0; c < C; ++c)
-        for (int g = 0; g < n_g32; ++g) {
-            a1d_off[(size_t)c * n_g32 + g] = (long long)n1d;
-            n1d += 128ull * pad64(2 * p->box[c].nx);
-        }
-    std::vector<uint16_t> a1d(n1d, 0);
-    for (int c = 0; c < C; ++c) {
-        const Box b = p->box[c];
-        const int K1 = 2 * b.nx;
-        for (int g = 0; g < n_g32; ++g) {
-            uint16_t* t = &a1d[a1d_off[(size_t)c * n_g32 + g]];
-            for (int r = 0; r < 128; ++r) {
-                const int q = r / 64, kx = 32 * g + r % 32;
-                if (kx >= N) continue;
-                for (int k = 0; k < K1; ++k) {
-                    const int x = b.x0 + (k % b.nx);
-                    double fr, fi;
-                    F(x, kx, &fr, &fi);
-                    const double v = q == 0 ? (k < b.nx ? fr : -fi) : (k < b.nx ? fi : fr);
-                    t[sw_off(r, k, 128)] = f16_bits(v);
-                }
-            }
-        }
-    }
-    p->tc.n_g32 = n_g32;
     // row-major stage-2 operand as packed FP16 pairs (lower K in the low half) for TMEM
     std::vector<long long> a2w_off((size_t)C * n_kb);
     size_t nw = 0;
@@ -2925,11 +2491,6 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a1p_off, a1p_off.size() * sizeof(long long));
     if (e == cudaSuccess)
         e = cudaMemcpy(p->tc.a1p_off, a1p_off.data(), a1p_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a1d, n1d * 2);
-    if (e == cudaSuccess) e = cudaMemcpy(p->tc.a1d, a1d.data(), n1d * 2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->tc.a1d_off, a1d_off.size() * sizeof(long long));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->tc.a1d_off, a1d_off.data(), a1d_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w, nw * 4);
     if (e == cudaSuccess) e = cudaMemcpy(p->tc.a2w, a2w.data(), nw * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2w_off, a2w_off.size() * sizeof(long long));
@@ -2947,9 +2508,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->tc.status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(p, e, "tensor path table upload");
-    p->dt.dft_bytes = (n1 + n2 + n1p + n1d) * 2 + nw * 4 +
-                      (a1_off.size() + a2_off.size() + a1p_off.size() + a1d_off.size() + a2w_off.size()) *
-                          sizeof(long long);
+    p->dt.dft_bytes = (n1 + n2 + n1p) * 2 + nw * 4 +
+                      (a1_off.size() + a2_off.size() + a1p_off.size() + a2w_off.size()) * sizeof(long long);
 
     // algorithmic work of the pruned DFT-as-GEMM per time sample (all channels, pols):
     // complex MACs  nyp*nxp*N (rows along x) + N*nyp*N (columns along y), 8 flops each
@@ -2961,7 +2521,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
     size_t stride = 0;
     for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
-    const int per_ch = n_kb * ((p->tc.ws || p->tc.ws4) ? n_gp : n_s);
+    const int per_ch = n_kb * (p->tc.ws ? n_gp : n_s);
     p->tc.cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
     p->tc.stride = stride;
     epic_status cst = dftgemm_set_chunk(p, kScratchBudget);
@@ -3108,18 +2668,14 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws4<0>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws4<1>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws4<2>, p->smem_optin);
-    if (p->sm_count > kWs3MaxBlocks) p->tc.ws4 = false;  // the split bookkeeping holds kWs3MaxBlocks blocks
-    p->tc.ws_variant = p->tc.ws ? 3 : p->tc.ws4 ? 4 : 0;
+    p->tc.ws_variant = p->tc.ws ? 3 : 0;
     if (p->tc.ws && p->sm_count > kWs3MaxBlocks) p->tc.ws_variant = 1;
-    if (p->sub > 0 && p->tc.ws_variant != 3 && p->tc.ws_variant != 4) {
+    if (p->sub > 0 && p->tc.ws_variant != 3) {
         p->last_error = "tensor path: sub-integrations need a control-warp kernel (occupied grid too large)";
         return EPIC_ERR_UNSUPPORTED;
     }
-    if ((p->tc.ws || p->tc.ws4) && e == cudaSuccess) {
-        const size_t n_items = (size_t)p->tc.cg * n_kb * std::max(n_gp, n_g32);
+    if (p->tc.ws && e == cudaSuccess) {
+        const size_t n_items = (size_t)p->tc.cg * n_kb * n_gp;
         e = cudaMalloc(&p->tc.partial, (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&p->tc.counters, n_items * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->tc.counters, 0, n_items * sizeof(int));
@@ -3251,31 +2807,11 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             a.sub = p->sub;
             a.iv0 = p->sub > 0 ? t0 / p->sub : 0;
             a.C = C;
-            const bool v4 = p->tc.ws_variant == 4;
-            const int items = ng * a.n_kb * (v4 ? p->tc.n_g32 : p->tc.ws ? p->tc.n_gp : a.n_s);
+            const int items = ng * a.n_kb * (p->tc.ws ? p->tc.n_gp : a.n_s);
             const int grid = std::min(items, p->sm_count);
-            ev_begin(p, v4 ? "k_dftgemm_ws4"
-                           : p->tc.ws ? (p->tc.ws_variant == 3 ? "k_dftgemm_ws3" : p->tc.ws_variant == 2 ? "k_dftgemm_ws2" : "k_dftgemm_ws")
-                                      : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
-            if (v4) {
-                MmaArgs a4 = a;
-                a4.n_g = p->tc.n_g32;
-                a4.a1p = p->tc.a1d;
-                a4.a1p_off = p->tc.a1d_off;
-                a4.sA1 = 0;
-                a4.sB1 = p->tc.ws4_sB1;
-                a4.sB2 = p->tc.ws4_sB2;
-                a4.b2_bytes = p->tc.ws4_b2_bytes;
-                a4.partial = p->tc.partial;
-                a4.counters = p->tc.counters;
-                const int sm4 = p->tc.ws4_smem;
-                if (p->sub > 0)
-                    k_dftgemm_ws4<2><<<grid, kWs4Threads, sm4, s>>>(a4);
-                else if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
-                    k_dftgemm_ws4<1><<<p->sm_count, kWs4Threads, sm4, s>>>(a4);
-                else
-                    k_dftgemm_ws4<0><<<grid, kWs4Threads, sm4, s>>>(a4);
-            } else if (p->tc.ws) {
+            ev_begin(p, p->tc.ws ? (p->tc.ws_variant == 3 ? "k_dftgemm_ws3" : p->tc.ws_variant == 2 ? "k_dftgemm_ws2" : "k_dftgemm_ws")
+                                 : p->tc.fast ? "k_dftgemm_mma_fast" : "k_dftgemm_mma", s);
+            if (p->tc.ws) {
                 a.n_g = p->tc.n_gp;
                 if (p->tc.ws_variant == 3) {
                     a.partial = p->tc.partial;

@@ -34,8 +34,8 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
     } else if (p->path == EPIC_PATH_FUSED_FP32) {
         knobs.push_back({"slab", {8, 16, 32}, p->slab, set_fused_slab});
     } else if (p->path == EPIC_PATH_DFTGEMM_FP16) {
-        if ((p->tc.ws || p->tc.ws4) && p->sub == 0) {  // sub-integrations: control-warp kernels, whole items
-            knobs.push_back({"mma_kernel", {1, 2, 3, 4}, p->tc.ws_variant, set_dft_kernel});
+        if (p->tc.ws && p->sub == 0) {  // sub-integrations use the control-warp kernel on whole items
+            knobs.push_back({"mma_kernel", {1, 2, 3}, p->tc.ws_variant, set_dft_kernel});
             knobs.push_back({"split", {-1, 0, 1}, p->tc.split, set_dft_split});
         }
         if (p->tc.grid_ps && p->tc.gtask)
