@@ -537,6 +537,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         tc::mbar_init(&bar_raw[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = tid; i < F * A; i += blockDim.x) sv[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // short passes read all F
     __syncthreads();
     if (w0 >= w1) return;
 
@@ -559,11 +560,12 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         fetch(w0, 0);
         pending = 1u;
     }
+    int4 b = make_int4(0, 0, 0, 0);  // box of the staged channel (read once per channel, not per pass)
     for (long long w = w0; w < w1;) {
         const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
         const long long wn = w + nf;
         const int c = a.c0 + cl;
-        const int4 b = a.box[c];
+        if (cl != staged) b = a.box[c];
         const int nxp = b.z, nyp = b.w, N1 = P * nyp;
         const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         const uint32_t tile_bytes = (uint32_t)N1 * pad64(2 * nxp) * 2;
@@ -616,19 +618,34 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
             const int2* lst = sell + tk.y + (s & 31);
-            for (int k = 0; k < n; ++k) {
-                const int2 cr = lst[32 * k];
+            auto apply = [&](int2 cr, const float4 (&v)[F]) {
                 const float wv = __int_as_float(cr.y);
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) {
-                    if (fi < nf) {
-                        const float4 v = sv[fi * A + cr.x];
-                        g[fi].x = fmaf(wv, v.x, g[fi].x);
-                        g[fi].y = fmaf(wv, v.y, g[fi].y);
-                        g[fi].z = fmaf(wv, v.z, g[fi].z);
-                        g[fi].w = fmaf(wv, v.w, g[fi].w);
-                    }
+                    g[fi].x = fmaf(wv, v[fi].x, g[fi].x);
+                    g[fi].y = fmaf(wv, v[fi].y, g[fi].y);
+                    g[fi].z = fmaf(wv, v[fi].z, g[fi].z);
+                    g[fi].w = fmaf(wv, v[fi].w, g[fi].w);
                 }
+            };
+            auto load = [&](int2 cr, float4 (&v)[F]) {  // frames past nf read stale but valid entries
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + cr.x];
+            };
+            int k = 0;
+            for (; k + 1 < n; k += 2) {  // two entries in flight, applied in list order
+                const int2 c0 = lst[32 * k], c1 = lst[32 * (k + 1)];
+                float4 v0[F], v1[F];
+                load(c0, v0);
+                load(c1, v1);
+                apply(c0, v0);
+                apply(c1, v1);
+            }
+            if (k < n) {
+                const int2 c0 = lst[32 * k];
+                float4 v0[F];
+                load(c0, v0);
+                apply(c0, v0);
             }
             const uint32_t o_rx = tile_half_off(y, x, N1), o_ix = tile_half_off(y, nxp + x, N1);
             const uint32_t o_ry = tile_half_off(nyp + y, x, N1), o_iy = tile_half_off(nyp + y, nxp + x, N1);
