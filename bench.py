@@ -186,8 +186,13 @@ def cpu_baseline(cfg, volt, seconds_hint: float = 20.0, n_time=None):
     oracle.image_cfg(cfg, volt[:T], chans=chans, threads=n_ch)
     dt = time.perf_counter() - t0
     units = cfg.grid_n ** 2 * n_ch * cfg.n_pol * T
+    t1 = time.perf_counter()                       # and one core on one of those channels
+    oracle.image_cfg(cfg, volt[:T], chans=chans[:1], threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": units / dt, "unit": UNIT, "cores": n_ch, "kind": "oracle",
-            "sample": f"{n_ch} of {cfg.n_chan} channels x {T} samples, OpenMP over channels ({dt:.2f} s)"}
+            "value_one_core": cfg.grid_n ** 2 * cfg.n_pol * T / dt1,
+            "sample": f"{n_ch} of {cfg.n_chan} channels x {T} samples, OpenMP over channels ({dt:.2f} s); "
+                      f"one core: 1 channel x {T} samples ({dt1:.2f} s)"}
 
 
 def run_reference(args, cfg, world, rank):

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import epic_synth as synth
+from gpu_common import assert_parity, oracle_image
 
 torch = pytest.importorskip("torch")
 
@@ -61,6 +62,11 @@ def test_each_block_same_alone_and_in_the_mix():
     assert 0 < st["p50_ms"] <= st["p99_ms"]
     for (si, v), o, ref in zip(blocks, outs, alone):
         assert np.array_equal(o.cpu().numpy(), ref), f"station {si}"
+    # a seeded sample of the served blocks against the FP64 oracle
+    for k in np.random.default_rng(5).choice(len(blocks), size=3, replace=False):
+        si, v = blocks[k]
+        cfg, path = stations[si]
+        assert_parity(outs[k].cpu().numpy(), oracle_image(cfg, v), path, f"served block {k} (station {si})")
     for p in plans:
         p.close()
 
