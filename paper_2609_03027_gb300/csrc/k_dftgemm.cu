@@ -131,23 +131,6 @@ __device__ __forceinline__ size_t sw_chunk(int r, int c, int R)
     return (size_t)(c >> 3) * ((size_t)R * 128) + (size_t)r * 128 + (((c & 7) ^ (r & 7)) << 4);
 }
 
-// Eight grid cells (x8*8 .. x8*8+7) of tile row R (of N1 rows) as two 16-byte
-// chunks: real parts at K chunk x8, imaginary parts at K chunk nxp/8 + x8.
-__device__ __forceinline__ void store_tile_row(uint8_t* tile, int R, int N1, int nxp, int x8, const float2 (&g)[8])
-{
-    uint4 re, im;
-    re.x = pack_h2(g[0].x, g[1].x);
-    re.y = pack_h2(g[2].x, g[3].x);
-    re.z = pack_h2(g[4].x, g[5].x);
-    re.w = pack_h2(g[6].x, g[7].x);
-    im.x = pack_h2(g[0].y, g[1].y);
-    im.y = pack_h2(g[2].y, g[3].y);
-    im.z = pack_h2(g[4].y, g[5].y);
-    im.w = pack_h2(g[6].y, g[7].y);
-    *reinterpret_cast<uint4*>(tile + sw_chunk(R, x8, N1)) = re;
-    *reinterpret_cast<uint4*>(tile + sw_chunk(R, (nxp >> 3) + x8, N1)) = im;
-}
-
 // 16 consecutive image pixels of one product: written, or added to what is there.
 __device__ __forceinline__ void store_pixels16(float* op, int nk, int accumulate, const float (&v)[16])
 {
@@ -191,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                                                            uint8_t* __restrict__ tiles,
                                                            unsigned long long tile_stride)
 {
-    extern __shared__ __align__(16) uint8_t gsm[];
+    extern __shared__ __align__(128) uint8_t gsm[];
     float4* sv = reinterpret_cast<float4*>(gsm);  // [F][A]: (re X, im X, re Y, im Y)
     const int cl = blockIdx.y, c = c0 + cl;
     const float4* jm = jones ? jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
@@ -315,7 +298,7 @@ __host__ __device__ inline size_t grid_ps_smem(int F, int A, int frame_bytes, in
 template <bool CPLX, int F>
 __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
 {
-    extern __shared__ __align__(16) uint8_t gsm[];
+    extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ uint64_t bar_raw[2];
     const int tid = threadIdx.x;
     const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
@@ -485,7 +468,8 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
 // first pass.  The (element, weight) entries of the 32 cells a warp handles together
 // are interleaved (entry k of lane l at 32 k + l), so a warp reads them as one
 // contiguous 256-byte row per step.
-constexpr int kGridBalThreads = 512;
+constexpr int kGridBalThreads = 512;                      // gridding threads
+constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that issues the bulk copies
 
 struct GridBalArgs {
     GridArgs g;
@@ -515,12 +499,17 @@ __device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
 }
 
 template <int F>
-__global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBalArgs ba)
+__global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalArgs ba)
 {
     const GridArgs& a = ba.g;
     extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ uint64_t bar_raw[2];
     const int tid = threadIdx.x;
+    // Threads 0..kGridBalThreads-1 grid; the first thread of the last warp issues every bulk
+    // copy (raw frames of the next pass, tile stores of the previous one) while the others
+    // work, so that no gridding thread waits for the copy engine to accept a copy.
+    const bool tma = tid == kGridBalThreads;
+    const int nthr = kGridBalThreads;
     const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
     const int APr = (AP + 15) & ~15;
     uint8_t* raw = gsm;                                                // [2][F][APr]
@@ -532,7 +521,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
 
     const long long W = (long long)a.n_ch * a.nt;
     const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
-    if (tid == 0) {
+    if (tma) {
         tc::mbar_init(&bar_raw[0], 1);
         tc::mbar_init(&bar_raw[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -545,7 +534,7 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         const int f = (int)(w % a.nt);
         return (int)min((long long)min(F, a.nt - f), w1 - w);
     };
-    auto fetch = [&](long long w, int b) {  // thread 0: raw bytes of the pass starting at w -> buffer b
+    auto fetch = [&](long long w, int b) {  // copy thread: raw bytes of the pass starting at w -> buffer b
         const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
         tc::mbar_expect_tx(&bar_raw[b], (uint32_t)(nf * AP));
         for (int i = 0; i < nf; ++i)
@@ -556,10 +545,21 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
     uint32_t ph = 0, pending = 0;
     int staged = -1, buf = 0, tb = 0, ntask = 0;
     bool ok = true;
-    if (a.bulk && tid == 0) {
+    if (a.bulk && tma) {
         fetch(w0, 0);
         pending = 1u;
     }
+    // tile stores of the last finished pass, issued by the copy thread one pass later
+    int d_nf = 0, d_f = 0, d_cl = 0, d_tb = 0;
+    uint32_t d_bytes = 0;
+    auto store_deferred = [&]() {
+        if (d_nf == 0) return;
+        for (int fi = 0; fi < d_nf; ++fi)
+            tc::bulk_s2g(a.tiles + ((size_t)(d_f + fi) * a.n_ch + d_cl) * a.tile_stride,
+                         stile + ((size_t)d_tb * F + fi) * ba.tile_max, d_bytes);
+        tc::bulk_commit();
+        d_nf = 0;
+    };
     int4 b = make_int4(0, 0, 0, 0);  // box of the staged channel (read once per channel, not per pass)
     for (long long w = w0; w < w1;) {
         const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
@@ -569,17 +569,16 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         const int nxp = b.z, nyp = b.w, N1 = P * nyp;
         const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         const uint32_t tile_bytes = (uint32_t)N1 * pad64(2 * nxp) * 2;
-        if (a.bulk && tid == 0 && wn < w1) {
-            fetch(wn, buf ^ 1);
-            pending |= 1u << (buf ^ 1);
-        }
         if (cl != staged) {  // new channel: zeroed tile buffers, its task list and entries
-            if (tid == 0) tc::bulk_wait_read<0>();
+            if (tma) {
+                store_deferred();
+                tc::bulk_wait_read<0>();
+            }
             __syncthreads();
             const int nz = (int)((2ull * F * ba.tile_max) >> 4);
             for (int i = tid; i < nz; i += blockDim.x) reinterpret_cast<uint4*>(stile)[i] = make_uint4(0, 0, 0, 0);
+            ntask = ba.task_off[c + 1] - ba.task_off[c];
             const int t0 = ba.task_off[c];
-            ntask = ba.task_off[c + 1] - t0;
             for (int i = tid; i < ntask; i += blockDim.x) stask[i] = ba.tasks[t0 + i];
             const int e0 = ba.ell_off[c], nell = ba.ell_off[c + 1] - e0;
             for (int i = tid; i < nell; i += blockDim.x) sell[i] = ba.ell[e0 + i];
@@ -595,22 +594,29 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
                 ok = false;
                 break;
             }
-            for (int i = tid; i < nf * A; i += blockDim.x) {
+            for (int i = tid; i < nf * A && tid < nthr; i += nthr) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
                 sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         } else {
-            for (int i = tid; i < nf * A; i += blockDim.x) {
+            for (int i = tid; i < nf * A && tid < nthr; i += nthr) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
                 sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
             }
         }
-        if (tid == 0) tc::bulk_wait_read<1>();  // the stores of the pass before last have read tile buffer tb
+        if (tma) {  // the previous pass's tiles go out; those of the pass before last have been read
+            store_deferred();
+            tc::bulk_wait_read<1>();
+        }
         __syncthreads();
+        if (a.bulk && tma && wn < w1) {  // raw frames of the next pass, while the others grid
+            fetch(wn, buf ^ 1);
+            pending |= 1u << (buf ^ 1);
+        }
         uint8_t* tset = stile + (size_t)tb * F * ba.tile_max;
-        for (int s = tid; s < ntask; s += blockDim.x) {
+        for (int s = tid; s < ntask && tid < nthr; s += nthr) {
             const int2 tk = stask[s];
             const int r = tk.x & 0xFFFFFF, n = (int)((unsigned)tk.x >> 24);
             const int y = r / nxp, x = r - y * nxp;
@@ -663,17 +669,19 @@ __global__ void __launch_bounds__(kGridBalThreads, 1) k_dftgemm_grid_bal(GridBal
         }
         tc::fence_proxy_async();  // tile writes -> visible to the bulk copies
         __syncthreads();
-        if (tid == 0) {
-            for (int fi = 0; fi < nf; ++fi)
-                tc::bulk_s2g(a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride, tset + (size_t)fi * ba.tile_max,
-                             tile_bytes);
-            tc::bulk_commit();
+        if (tma) {  // stored at the next pass (or after the loop)
+            d_nf = nf;
+            d_f = f;
+            d_cl = cl;
+            d_tb = tb;
+            d_bytes = tile_bytes;
         }
         w = wn;
         buf ^= 1;
         tb ^= 1;
     }
-    if (tid == 0) {
+    if (tma) {
+        if (ok) store_deferred();
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // tile stores complete
         if (!ok) {
             for (int b2 = 0; b2 < 2; ++b2)
@@ -2279,7 +2287,7 @@ static epic_status grid_bal_config(epic_plan_s* p, int F)
     e = allow_max_smem(fn, p->smem_optin);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_bal)");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridBalThreads, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridBalBlock, bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_dftgemm_grid_bal)");
     if (occ < 1) return EPIC_ERR_UNSUPPORTED;
     p->tc.grid_frames = F;
@@ -2778,9 +2786,9 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     ba.max_tasks = p->tc.gtask_max;
                     ba.max_ell = p->tc.gell_max;
                     ba.tile_max = (unsigned)p->tc.stride;
-                    if (F == 4) k_dftgemm_grid_bal<4><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
-                    else if (F == 2) k_dftgemm_grid_bal<2><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
-                    else k_dftgemm_grid_bal<1><<<gb, kGridBalThreads, p->tc.grid_smem, s>>>(ba);
+                    if (F == 4) k_dftgemm_grid_bal<4><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
+                    else if (F == 2) k_dftgemm_grid_bal<2><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
+                    else k_dftgemm_grid_bal<1><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
                 } else {
 #define EPIC_GRID_PS_LAUNCH(CX, FF) k_dftgemm_grid_ps<CX, FF><<<gb, kThreads, p->tc.grid_smem, s>>>(g)
                 if (p->tc.grid_cplx) {
