@@ -55,7 +55,7 @@ struct TcState {
     int grid_max_cells = 0;        // largest occupied box (cells)
     int grid_max_list = 0;         // (cell, element) entries per channel
     int grid_variant = 1;          // 1: persistent row-major gather, 2: balanced task lists
-    int2* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
+    int4* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list
     int2* gell = nullptr;          // balanced gridding: interleaved (element, weight) entries

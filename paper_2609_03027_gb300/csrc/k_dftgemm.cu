@@ -473,7 +473,8 @@ constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that is
 
 struct GridBalArgs {
     GridArgs g;
-    const int2* tasks;      // per channel: (cell | group's longest list << 24, group's first entry)
+    const int4* tasks;      // per channel: (cell | group's longest list << 24, group's first entry,
+                            //  tile byte offsets of the cell's re X and im X halves)
     const int* task_off;    // [C + 1]
     const int2* ell;        // per channel: (element, weight bits), 32 lanes interleaved per group
     const int* ell_off;     // [C + 1]
@@ -489,11 +490,11 @@ __host__ __device__ inline size_t grid_bal_smem(int F, int A, int frame_bytes, i
     size_t b = 2ull * F * ap + 16ull * F * A;  // raw voltages, unpacked voltages
     b = (b + 127) & ~(size_t)127;
     b += 2ull * F * tile_max;                  // tile buffers
-    b += 8ull * max_tasks + 8ull * max_list;   // task list, (element, weight) entries
+    b += 16ull * max_tasks + 8ull * max_list;  // task list, (element, weight) entries
     return b;
 }
 
-__device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
+__host__ __device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
 {
     return (uint32_t)((k >> 6) * (N1 * 128) + R * 128 + ((((k >> 3) & 7) ^ (R & 7)) << 4) + ((k & 7) << 1));
 }
@@ -516,8 +517,8 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
     float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);         // [F][A]
     const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
     uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
-    int2* stask = reinterpret_cast<int2*>(stile + 2ull * F * ba.tile_max);
-    int2* sell = stask + ba.max_tasks;
+    int4* stask = reinterpret_cast<int4*>(stile + 2ull * F * ba.tile_max);
+    int2* sell = reinterpret_cast<int2*>(stask + ba.max_tasks);
 
     const long long W = (long long)a.n_ch * a.nt;
     const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
@@ -617,9 +618,8 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
         }
         uint8_t* tset = stile + (size_t)tb * F * ba.tile_max;
         for (int s = tid; s < ntask && tid < nthr; s += nthr) {
-            const int2 tk = stask[s];
-            const int r = tk.x & 0xFFFFFF, n = (int)((unsigned)tk.x >> 24);
-            const int y = r / nxp, x = r - y * nxp;
+            const int4 tk = stask[s];
+            const int n = (int)((unsigned)tk.x >> 24);
             float4 g[F];
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -653,8 +653,10 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
                 load(c0, v0);
                 apply(c0, v0);
             }
-            const uint32_t o_rx = tile_half_off(y, x, N1), o_ix = tile_half_off(y, nxp + x, N1);
-            const uint32_t o_ry = tile_half_off(nyp + y, x, N1), o_iy = tile_half_off(nyp + y, nxp + x, N1);
+            // rows nyp + y (pol Y) sit nyp rows below rows y within every 64-column panel, with the
+            // same swizzle phase (nyp is a multiple of 8)
+            const uint32_t o_rx = (uint32_t)tk.z, o_ix = (uint32_t)tk.w;
+            const uint32_t o_ry = o_rx + (uint32_t)nyp * 128, o_iy = o_ix + (uint32_t)nyp * 128;
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) {
                 if (fi >= nf) break;
@@ -2576,7 +2578,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
         // Cells of a channel sorted by contribution count; groups of 32 consecutive cells
         // (the lanes of one warp) store their (element, weight) entries interleaved, entry k
         // of lane l at 32 k + l, padded with zero weights to the group's longest list.
-        std::vector<int2> tasks, ell;
+        std::vector<int4> tasks;
+        std::vector<int2> ell;
         std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
         bool fits = true;
         int tmax = 0, emax = 0;
@@ -2605,10 +2608,14 @@ epic_status dftgemm_setup(epic_plan_s* p)
                         }
                         ell.push_back(en);
                     }
+                const Box bx = p->box[c];
+                const int n1 = p->P * bx.ny;
                 for (int l = 0; l < members; ++l) {
                     const int r = idx[g0 + l];
                     if (r >= (1 << 24)) fits = false;
-                    tasks.push_back(make_int2(r | (nmax << 24), base));
+                    const int y = r / bx.nx, x = r - y * bx.nx;
+                    tasks.push_back(make_int4(r | (nmax << 24), base, (int)tile_half_off(y, x, n1),
+                                              (int)tile_half_off(y, bx.nx + x, n1)));
                 }
             }
             tmax = std::max(tmax, (int)idx.size());
@@ -2617,8 +2624,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
         toff[C] = (int)tasks.size();
         eoff[C] = (int)ell.size();
         if (fits && !tasks.empty()) {
-            e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int2));
-            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int2),
+            e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int4));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int4),
                                                  cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gtask_off, toff.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask_off, toff.data(), toff.size() * sizeof(int),
@@ -2653,7 +2660,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     if (kst != EPIC_OK) return kst;
                 }
             } else {
-                p->dt.dft_bytes += (tasks.size() + ell.size()) * sizeof(int2) + (toff.size() + eoff.size()) * sizeof(int);
+                p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell.size() * sizeof(int2) +
+                                   (toff.size() + eoff.size()) * sizeof(int);
             }
         }
     }
