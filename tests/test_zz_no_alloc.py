@@ -64,3 +64,20 @@ def test_static_scratch_rejects_blocks_beyond_its_size():
         st = f(plan._h, v.data_ptr(), 2, torch.cuda.current_stream().cuda_stream, out.data_ptr(), 0)
         assert st == 7                                          # EPIC_ERR_UNSUPPORTED
         assert "MiB" in L.epic_last_error(plan._h).decode()
+
+
+@pytest.mark.gpu
+def test_static_scratch_rejects_formats_it_does_not_take():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    import dataclasses
+    L, f = _entry()
+    base = synth.small_config(n_ant=16, n_chan=2, n_pol=2, grid_n=32, gcf_k=3, n_time=4, seed=93, diameter_m=8.0)
+    variants = [dataclasses.replace(base, input_bits=8), dataclasses.replace(base, sub_int=2),
+                dataclasses.replace(base, jones=synth.make_jones(base, seed=1))]
+    for cfg in variants:
+        with E.Plan.from_config(cfg, path="plain") as plan:
+            v = torch.from_numpy(synth.make_voltages(cfg)).cuda()
+            out = torch.zeros(plan.image_shape(cfg.n_time), device="cuda")
+            st = f(plan._h, v.data_ptr(), cfg.n_time, torch.cuda.current_stream().cuda_stream, out.data_ptr(), 0)
+            assert st == 7, L.epic_last_error(plan._h).decode()        # EPIC_ERR_UNSUPPORTED
