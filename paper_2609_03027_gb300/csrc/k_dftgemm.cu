@@ -40,7 +40,7 @@ namespace epic {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr size_t kScratchBudget = 768ull << 20;  // grid tiles of one (channel group, time chunk)
+constexpr size_t kScratchBudget = 3072ull << 20;  // grid tiles of one (channel group, time chunk)
 constexpr long long kWaitBudget = 4000000000LL;  // clock cycles before a wait gives up (~2 s)
 constexpr int kGridFramesPerBlock = 8;            // frames gridded per block (cell lists read once)
 

@@ -42,7 +42,7 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
             knobs.push_back({"grid_kernel", {1, 2}, p->tc.grid_variant, set_dft_grid_kernel});
         if (p->tc.grid_ps || p->tc.gtask)
             knobs.push_back({"grid_frames", {1, 2, 4, 8}, p->tc.grid_frames, set_dft_frames});
-        knobs.push_back({"chunk_mb", {48, 96, 192, 384, 768}, budget_mb, set_dft_chunk});
+        knobs.push_back({"chunk_mb", {96, 192, 384, 768, 1536, 3072}, budget_mb, set_dft_chunk});
     }
     return knobs;
 }
