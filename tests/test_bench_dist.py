@@ -63,3 +63,21 @@ def test_recorded_traffic_only_for_the_captured_launch_configuration():
     import dataclasses
     assert bench.recorded_traffic("k_dftgemm_ws3", 2, 250, dataclasses.replace(cfg, input_bits=8),
                                   dict(rec["params"])) is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the --impl reference arm runs the FP64 oracle on the host cores, no GPU needed
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1", "--config", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["config"]["workload"].startswith("tiny")
