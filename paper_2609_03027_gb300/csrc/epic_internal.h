@@ -145,6 +145,7 @@ epic_status build_geometry(epic_plan_s* p, std::string* err);
 void build_csr(const epic_plan_s* p, std::vector<int>& cell_off, std::vector<int>& cell_ptr,
                std::vector<int>& contrib_e, std::vector<float2>& contrib_w);
 void build_twiddles(int N, std::vector<float2>& tw);
+void order_warp_entries(const std::vector<std::vector<int2>>& cells, int nmax, int2* out);
 
 // api.cu helpers used by the kernels' launch code
 // Let kernel `fn` take as much dynamic shared memory as the device allows (its

@@ -2575,9 +2575,11 @@ epic_status dftgemm_setup(epic_plan_s* p)
         std::vector<int> coff, cptr, ce;
         std::vector<float2> cw;
         build_csr(p, coff, cptr, ce, cw);
-        // Cells of a channel sorted by contribution count; groups of 32 consecutive cells
-        // (the lanes of one warp) store their (element, weight) entries interleaved, entry k
-        // of lane l at 32 k + l, padded with zero weights to the group's longest list.
+        // Cells of a channel sorted by contribution count (cells of equal count in Morton
+        // order, so that a warp's cells are near one another and share elements); groups of
+        // 32 consecutive cells (the lanes of one warp) store their (element, weight) entries
+        // interleaved, entry k of lane l at 32 k + l, padded with zero weights to the
+        // group's longest list, in the order order_warp_entries picks.
         std::vector<int4> tasks;
         std::vector<int2> ell;
         std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
@@ -2591,23 +2593,30 @@ epic_status dftgemm_setup(epic_plan_s* p)
             std::vector<int> idx;
             for (int r = 0; r < ncell; ++r)
                 if (ptr[r + 1] > ptr[r]) idx.push_back(r);
-            std::stable_sort(idx.begin(), idx.end(),
-                             [&](int u, int v) { return ptr[u + 1] - ptr[u] > ptr[v + 1] - ptr[v]; });
+            const int bnx = p->box[c].nx;
+            auto morton = [bnx](int r) {
+                const unsigned x = (unsigned)(r % bnx), y = (unsigned)(r / bnx);
+                unsigned m = 0;
+                for (int bit = 0; bit < 12; ++bit) m |= ((x >> bit) & 1u) << (2 * bit) | ((y >> bit) & 1u) << (2 * bit + 1);
+                return m;
+            };
+            std::stable_sort(idx.begin(), idx.end(), [&](int u, int v) {
+                const int nu = ptr[u + 1] - ptr[u], nv = ptr[v + 1] - ptr[v];
+                return nu != nv ? nu > nv : morton(u) < morton(v);
+            });
             for (size_t g0 = 0; g0 < idx.size(); g0 += 32) {
                 const int members = (int)std::min<size_t>(32, idx.size() - g0);
                 const int nmax = ptr[idx[g0] + 1] - ptr[idx[g0]];
                 const int base = (int)ell.size() - eoff[c];
                 if (nmax > 255) fits = false;
-                for (int k = 0; k < nmax; ++k)
-                    for (int l = 0; l < 32; ++l) {
-                        int2 en = make_int2(0, __float_as_int_host(0.f));
-                        if (l < members) {
-                            const int r = idx[g0 + l];
-                            if (k < ptr[r + 1] - ptr[r])
-                                en = make_int2(ce[ptr[r] + k], __float_as_int_host(cw[ptr[r] + k].x));
-                        }
-                        ell.push_back(en);
-                    }
+                std::vector<std::vector<int2>> lists(members);
+                for (int l = 0; l < members; ++l) {
+                    const int r = idx[g0 + l];
+                    for (int k = ptr[r]; k < ptr[r + 1]; ++k)
+                        lists[l].push_back(make_int2(ce[k], __float_as_int_host(cw[k].x)));
+                }
+                ell.resize(ell.size() + 32ull * nmax);
+                order_warp_entries(lists, nmax, ell.data() + (ell.size() - 32ull * nmax));
                 const Box bx = p->box[c];
                 const int n1 = p->P * bx.ny;
                 for (int l = 0; l < members; ++l) {

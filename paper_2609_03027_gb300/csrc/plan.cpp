@@ -171,4 +171,79 @@ void build_twiddles(int N, std::vector<float2>& tw)
     }
 }
 
+// Interleaves the (element, weight) entries of one warp's cells for the balanced
+// gridding kernel: entry k of lane l goes to out[32 k + l], every lane padded to nmax
+// entries with zero weights.  A cell's sum does not depend on the order of its
+// entries beyond FP32 rounding, so the order is chosen for the shared-memory gather:
+// at step k the lanes of a warp read the 16-byte voltages of their k-th elements,
+// and 8 lanes that ask for different elements in the same 16-byte bank quad
+// (element mod 8) serialise.  Per step and per group of 8 lanes, lanes that must take
+// an entry now come first, then those with the fewest distinct quads left; each
+// takes an element another lane already reads (a broadcast), else one on an unused
+// quad (the quad most in demand among the group's remaining entries), else, if it
+// has slack, a padding entry on an element already read.
+void order_warp_entries(const std::vector<std::vector<int2>>& cells, int nmax, int2* out)
+{
+    const int members = (int)cells.size();
+    std::vector<std::vector<int2>> rem(cells);
+    for (int k = 0; k < nmax; ++k) {
+        const int left = nmax - k;
+        for (int q0 = 0; q0 < 32; q0 += 8) {
+            int demand[8] = {0, 0, 0, 0, 0, 0, 0, 0}, used[8], lanes[8], key[8], nl = 0, first = -1;
+            bool pad[8] = {false, false, false, false, false, false, false, false};
+            for (int q = 0; q < 8; ++q) used[q] = -1;
+            for (int l = q0; l < q0 + 8 && l < members; ++l) {
+                unsigned quads = 0;
+                for (const int2& en : rem[l]) {
+                    demand[en.x & 7]++;
+                    quads |= 1u << (en.x & 7);
+                }
+                int nq = 0;
+                for (int q = 0; q < 8; ++q) nq += (quads >> q) & 1u;
+                key[nl] = ((int)rem[l].size() == left ? 0 : 16) + (rem[l].empty() ? 15 : nq);
+                lanes[nl++] = l;
+            }
+            for (int i = 1; i < nl; ++i)  // stable insertion sort by key
+                for (int j = i; j > 0 && key[j - 1] > key[j]; --j) {
+                    std::swap(key[j - 1], key[j]);
+                    std::swap(lanes[j - 1], lanes[j]);
+                }
+            for (int i = 0; i < nl; ++i) {
+                std::vector<int2>& r = rem[lanes[i]];
+                int pick = -1;
+                for (int j = 0; j < (int)r.size() && pick < 0; ++j)
+                    if (used[r[j].x & 7] == r[j].x) pick = j;
+                if (pick < 0) {
+                    int best = -1;
+                    for (int j = 0; j < (int)r.size(); ++j) {
+                        const int q = r[j].x & 7;
+                        if (used[q] < 0 && demand[q] > best) {
+                            best = demand[q];
+                            pick = j;
+                        }
+                    }
+                }
+                if (pick < 0) {
+                    if ((int)r.size() < left) {  // empty, or slack left: pad this step
+                        pad[i] = true;
+                        continue;
+                    }
+                    pick = 0;
+                }
+                const int2 en = r[pick];
+                if (used[en.x & 7] < 0) {
+                    used[en.x & 7] = en.x;
+                    if (first < 0) first = en.x;
+                }
+                out[32 * k + lanes[i]] = en;
+                r.erase(r.begin() + pick);
+            }
+            const int2 zero = make_int2(first < 0 ? 0 : first, 0);  // weight +0.0f
+            for (int i = 0; i < nl; ++i)
+                if (pad[i]) out[32 * k + lanes[i]] = zero;
+            for (int l = std::max(q0, members); l < q0 + 8; ++l) out[32 * k + l] = zero;
+        }
+    }
+}
+
 }  // namespace epic

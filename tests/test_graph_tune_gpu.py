@@ -88,20 +88,32 @@ def test_gridding_frames_per_pass_bitwise_identical():
         first = next(iter(outs.values()))
         for F, o in outs.items():
             assert np.array_equal(o, first), F
-        # both gridding kernels (row-major walk, length-sorted cell lists) alike
+        # both gridding kernels (row-major walk in element order; length-sorted cell lists in
+        # an order chosen for the shared-memory banks) alike up to FP32 summation order, and
+        # each bitwise the same for every number of frames per pass
+        last = first
         for gk in (1, 2):
             try:
                 plan.set_param("grid_kernel", gk)
             except E.EpicError as ex:
                 assert ex.status in (7, 8)
                 continue
-            assert np.array_equal(plan.image(v).cpu().numpy(), first), gk
+            o = plan.image(v).cpu().numpy()
+            assert rel_errors(o, first.astype(np.float64)).max() <= 1e-5, gk
+            for F in (1, 2):
+                try:
+                    plan.set_param("grid_frames", F)
+                except E.EpicError as ex:
+                    assert ex.status == 7
+                    continue
+                assert np.array_equal(plan.image(v).cpu().numpy(), o), (gk, F)
+            last = o
         # voltage block at an address that is not 16-byte aligned: no bulk copies
         raw = torch.zeros(v.numel() + 16, dtype=torch.uint8, device="cuda")
         va = raw[1:1 + v.numel()].view(v.shape)
         va.copy_(v)
         assert va.data_ptr() % 16 == 1
-        assert np.array_equal(plan.image(va).cpu().numpy(), first)
+        assert np.array_equal(plan.image(va).cpu().numpy(), last)
     assert_parity(first, oracle_image(cfg, vn), "dftgemm", "frames per pass")
 
 
