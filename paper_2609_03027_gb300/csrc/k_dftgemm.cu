@@ -467,7 +467,10 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
 // buffered across passes; cells no task touches stay zero from the channel's
 // first pass.  The (element, weight) entries of the 32 cells a warp handles together
 // are interleaved (entry k of lane l at 32 k + l), so a warp reads them as one
-// contiguous 256-byte row per step.
+// contiguous 256-byte row per step.  With H the unpacked voltages are held as FP16
+// pairs, the F frames of an element side by side (F x 8 bytes: X, Y of frame 0, ...),
+// so one 16-byte load per entry serves two frames; 4- and 8-bit samples are exact in
+// FP16, so the sums are bitwise those of the FP32 form (which polarisation mixing uses).
 constexpr int kGridBalThreads = 512;                      // gridding threads
 constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that issues the bulk copies
 
@@ -499,7 +502,7 @@ __host__ __device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
     return (uint32_t)((k >> 6) * (N1 * 128) + R * 128 + ((((k >> 3) & 7) ^ (R & 7)) << 4) + ((k & 7) << 1));
 }
 
-template <int F>
+template <int F, bool H>
 __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalArgs ba)
 {
     const GridArgs& a = ba.g;
@@ -514,7 +517,8 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
     const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
     const int APr = (AP + 15) & ~15;
     uint8_t* raw = gsm;                                                // [2][F][APr]
-    float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);         // [F][A]
+    float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);         // [F][A] (FP32) or [A][F] (H)
+    uint2* svh = reinterpret_cast<uint2*>(sv);
     const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
     uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
     int4* stask = reinterpret_cast<int4*>(stile + 2ull * F * ba.tile_max);
@@ -598,13 +602,17 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             for (int i = tid; i < nf * A && tid < nthr; i += nthr) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = raw + (size_t)(buf * F + fi) * APr;
-                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
+                const float4 q = load_quad(fr, e, P, a.bits, jm);
+                if (H) svh[e * F + fi] = make_uint2(pack_h2(q.x, q.y), pack_h2(q.z, q.w));
+                else sv[fi * A + e] = q;
             }
         } else {
             for (int i = tid; i < nf * A && tid < nthr; i += nthr) {
                 const int fi = i / A, e = i - fi * A;
                 const uint8_t* fr = a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
-                sv[fi * A + e] = load_quad(fr, e, P, a.bits, jm);
+                const float4 q = load_quad(fr, e, P, a.bits, jm);
+                if (H) svh[e * F + fi] = make_uint2(pack_h2(q.x, q.y), pack_h2(q.z, q.w));
+                else sv[fi * A + e] = q;
             }
         }
         if (tma) {  // the previous pass's tiles go out; those of the pass before last have been read
@@ -635,8 +643,29 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
                 }
             };
             auto load = [&](int2 cr, float4 (&v)[F]) {  // frames past nf read stale but valid entries
+                if constexpr (H) {
+                    uint2 h[F];
+                    if constexpr (F == 1) {
+                        h[0] = svh[cr.x];
+                    } else {
+                        const uint4* q = reinterpret_cast<const uint4*>(svh + cr.x * F);
 #pragma unroll
-                for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + cr.x];
+                        for (int j = 0; j < F / 2; ++j) {
+                            const uint4 u = q[j];
+                            h[2 * j] = make_uint2(u.x, u.y);
+                            h[2 * j + 1] = make_uint2(u.z, u.w);
+                        }
+                    }
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) {
+                        const float2 x = __half22float2(*reinterpret_cast<const __half2*>(&h[fi].x));
+                        const float2 y = __half22float2(*reinterpret_cast<const __half2*>(&h[fi].y));
+                        v[fi] = make_float4(x.x, x.y, y.x, y.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + cr.x];
+                }
             };
             int k = 0;
             for (; k + 1 < n; k += 2) {  // two entries in flight, applied in list order
@@ -2280,8 +2309,12 @@ static epic_status grid_bal_config(epic_plan_s* p, int F)
     if (!p->tc.gtask || (F != 1 && F != 2 && F != 4)) return EPIC_ERR_UNSUPPORTED;
     const size_t bytes =
         grid_bal_smem(F, p->A, p->A * p->P * (p->bits / 4), p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride);
-    const void* fn = F == 4 ? (const void*)k_dftgemm_grid_bal<4>
-                   : F == 2 ? (const void*)k_dftgemm_grid_bal<2> : (const void*)k_dftgemm_grid_bal<1>;
+    // FP16-pair voltages (H) unless polarisation mixing makes them non-integer
+    const bool H = p->jones.empty();
+    const void* fn = H ? (F == 4 ? (const void*)k_dftgemm_grid_bal<4, true>
+                             : F == 2 ? (const void*)k_dftgemm_grid_bal<2, true> : (const void*)k_dftgemm_grid_bal<1, true>)
+                       : (F == 4 ? (const void*)k_dftgemm_grid_bal<4, false>
+                             : F == 2 ? (const void*)k_dftgemm_grid_bal<2, false> : (const void*)k_dftgemm_grid_bal<1, false>);
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_bal)");
@@ -2803,9 +2836,16 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     ba.max_tasks = p->tc.gtask_max;
                     ba.max_ell = p->tc.gell_max;
                     ba.tile_max = (unsigned)p->tc.stride;
-                    if (F == 4) k_dftgemm_grid_bal<4><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
-                    else if (F == 2) k_dftgemm_grid_bal<2><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
-                    else k_dftgemm_grid_bal<1><<<gb, kGridBalBlock, p->tc.grid_smem, s>>>(ba);
+                    const size_t sm = p->tc.grid_smem;
+                    if (p->jones.empty()) {  // FP16-pair voltages (exact for unmixed samples)
+                        if (F == 4) k_dftgemm_grid_bal<4, true><<<gb, kGridBalBlock, sm, s>>>(ba);
+                        else if (F == 2) k_dftgemm_grid_bal<2, true><<<gb, kGridBalBlock, sm, s>>>(ba);
+                        else k_dftgemm_grid_bal<1, true><<<gb, kGridBalBlock, sm, s>>>(ba);
+                    } else {
+                        if (F == 4) k_dftgemm_grid_bal<4, false><<<gb, kGridBalBlock, sm, s>>>(ba);
+                        else if (F == 2) k_dftgemm_grid_bal<2, false><<<gb, kGridBalBlock, sm, s>>>(ba);
+                        else k_dftgemm_grid_bal<1, false><<<gb, kGridBalBlock, sm, s>>>(ba);
+                    }
                 } else {
 #define EPIC_GRID_PS_LAUNCH(CX, FF) k_dftgemm_grid_ps<CX, FF><<<gb, kThreads, p->tc.grid_smem, s>>>(g)
                 if (p->tc.grid_cplx) {
