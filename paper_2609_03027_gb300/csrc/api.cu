@@ -61,7 +61,8 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.partial);
     cudaFree(p->tc.counters);
     cudaFree(p->tc.gtask_off);
-    cudaFree(p->tc.gell);
+    cudaFree(p->tc.gell_e);
+    cudaFree(p->tc.gell_w);
     cudaFree(p->tc.gell_off);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);

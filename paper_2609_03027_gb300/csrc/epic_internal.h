@@ -58,7 +58,8 @@ struct TcState {
     int4* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list
-    int2* gell = nullptr;          // balanced gridding: interleaved (element, weight) entries
+    int* gell_e = nullptr;         // balanced gridding: interleaved entries, element
+    float2* gell_w = nullptr;      //   and (weight at x, weight at x + 1) of a cell pair
     int* gell_off = nullptr;       // [C + 1]
     int gell_max = 0;              // largest entry list (with padding)
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2

@@ -458,28 +458,32 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
     }
 }
 
-// Balanced gridding kernel (real GCF weights): the gather of k_dftgemm_grid_ps,
-// but each thread works on single non-empty cells taken from a per-channel task
-// list sorted by contribution count, so the 32 lanes of a warp walk lists of
-// nearly equal length (a row-major walk keeps about 40% of the lanes busy), and
-// the F frames of a pass are assembled in shared-memory tiles that the TMA
-// engine then stores with one bulk copy per frame.  Tile buffers are double
-// buffered across passes; cells no task touches stay zero from the channel's
-// first pass.  The (element, weight) entries of the 32 cells a warp handles together
-// are interleaved (entry k of lane l at 32 k + l), so a warp reads them as one
-// contiguous 256-byte row per step.  With H the unpacked voltages are held as FP16
-// pairs, the F frames of an element side by side (F x 8 bytes: X, Y of frame 0, ...),
-// so one 16-byte load per entry serves two frames; 4- and 8-bit samples are exact in
-// FP16, so the sums are bitwise those of the FP32 form (which polarisation mixing uses).
+// Balanced gridding kernel (real GCF weights).  A task is a pair of horizontally
+// adjacent cells (x even, x + 1) of a channel's box: its list holds every element
+// whose footprint covers either cell, with the two weights (one of them zero at a
+// footprint's edge), so each voltage read serves both cells and the two FP16 results
+// of a tile row leave as one 32-bit word.  Tasks are taken from a per-channel list
+// sorted by entry count, so the 32 lanes of a warp walk lists of nearly equal length
+// (a row-major walk keeps about 40% of the lanes busy), and the F frames of a pass are
+// assembled in shared-memory tiles that the TMA engine then stores with one bulk copy
+// per frame.  Tile buffers are double buffered across passes; cells no task touches
+// stay zero from the channel's first pass.  The entries of the 32 tasks a warp handles
+// together are interleaved (entry k of lane l at 32 k + l: elements as one 128-byte row,
+// weight pairs as one 256-byte row per step).  With H the unpacked voltages are held
+// as FP16 pairs, the F frames of an element side by side (F x 8 bytes: X, Y of frame
+// 0, ...), so one 16-byte load per entry serves two frames; 4- and 8-bit samples are
+// exact in FP16, so the sums are bitwise those of the FP32 form (which polarisation
+// mixing uses).
 constexpr int kGridBalThreads = 512;                      // gridding threads
 constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that issues the bulk copies
 
 struct GridBalArgs {
     GridArgs g;
-    const int4* tasks;      // per channel: (cell | group's longest list << 24, group's first entry,
-                            //  tile byte offsets of the cell's re X and im X halves)
+    const int4* tasks;      // per channel: (cell pair | group's longest list << 24, group's first
+                            //  entry, tile byte offsets of the pair's re X and im X words)
     const int* task_off;    // [C + 1]
-    const int2* ell;        // per channel: (element, weight bits), 32 lanes interleaved per group
+    const int* ell_e;       // per channel: element of each entry, 32 lanes interleaved per group
+    const float2* ell_w;    // per channel: (weight at x, weight at x + 1) of each entry
     const int* ell_off;     // [C + 1]
     int max_tasks;          // largest task count of a channel
     int max_ell;            // largest entry count of a channel (with padding)
@@ -493,7 +497,7 @@ __host__ __device__ inline size_t grid_bal_smem(int F, int A, int frame_bytes, i
     size_t b = 2ull * F * ap + 16ull * F * A;  // raw voltages, unpacked voltages
     b = (b + 127) & ~(size_t)127;
     b += 2ull * F * tile_max;                  // tile buffers
-    b += 16ull * max_tasks + 8ull * max_list;  // task list, (element, weight) entries
+    b += 16ull * max_tasks + 12ull * max_list;  // task list, entries (weight pairs, elements)
     return b;
 }
 
@@ -522,7 +526,8 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
     const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
     uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
     int4* stask = reinterpret_cast<int4*>(stile + 2ull * F * ba.tile_max);
-    int2* sell = reinterpret_cast<int2*>(stask + ba.max_tasks);
+    float2* sell_w = reinterpret_cast<float2*>(stask + ba.max_tasks);
+    int* sell_e = reinterpret_cast<int*>(sell_w + ba.max_ell);
 
     const long long W = (long long)a.n_ch * a.nt;
     const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
@@ -586,7 +591,10 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             const int t0 = ba.task_off[c];
             for (int i = tid; i < ntask; i += blockDim.x) stask[i] = ba.tasks[t0 + i];
             const int e0 = ba.ell_off[c], nell = ba.ell_off[c + 1] - e0;
-            for (int i = tid; i < nell; i += blockDim.x) sell[i] = ba.ell[e0 + i];
+            for (int i = tid; i < nell; i += blockDim.x) {
+                sell_w[i] = ba.ell_w[e0 + i];
+                sell_e[i] = ba.ell_e[e0 + i];
+            }
             staged = cl;
         }
         if (a.bulk) {
@@ -628,27 +636,34 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
         for (int s = tid; s < ntask && tid < nthr; s += nthr) {
             const int4 tk = stask[s];
             const int n = (int)((unsigned)tk.x >> 24);
-            float4 g[F];
+            float4 g[F], h1[F];  // cells x and x + 1
 #pragma unroll
-            for (int fi = 0; fi < F; ++fi) g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int2* lst = sell + tk.y + (s & 31);
-            auto apply = [&](int2 cr, const float4 (&v)[F]) {
-                const float wv = __int_as_float(cr.y);
+            for (int fi = 0; fi < F; ++fi) {
+                g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
+                h1[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const int* le = sell_e + tk.y + (s & 31);
+            const float2* lw = sell_w + tk.y + (s & 31);
+            auto apply = [&](float2 w, const float4 (&v)[F]) {
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) {
-                    g[fi].x = fmaf(wv, v[fi].x, g[fi].x);
-                    g[fi].y = fmaf(wv, v[fi].y, g[fi].y);
-                    g[fi].z = fmaf(wv, v[fi].z, g[fi].z);
-                    g[fi].w = fmaf(wv, v[fi].w, g[fi].w);
+                    g[fi].x = fmaf(w.x, v[fi].x, g[fi].x);
+                    g[fi].y = fmaf(w.x, v[fi].y, g[fi].y);
+                    g[fi].z = fmaf(w.x, v[fi].z, g[fi].z);
+                    g[fi].w = fmaf(w.x, v[fi].w, g[fi].w);
+                    h1[fi].x = fmaf(w.y, v[fi].x, h1[fi].x);
+                    h1[fi].y = fmaf(w.y, v[fi].y, h1[fi].y);
+                    h1[fi].z = fmaf(w.y, v[fi].z, h1[fi].z);
+                    h1[fi].w = fmaf(w.y, v[fi].w, h1[fi].w);
                 }
             };
-            auto load = [&](int2 cr, float4 (&v)[F]) {  // frames past nf read stale but valid entries
+            auto load = [&](int el, float4 (&v)[F]) {  // frames past nf read stale but valid entries
                 if constexpr (H) {
                     uint2 h[F];
                     if constexpr (F == 1) {
-                        h[0] = svh[cr.x];
+                        h[0] = svh[el];
                     } else {
-                        const uint4* q = reinterpret_cast<const uint4*>(svh + cr.x * F);
+                        const uint4* q = reinterpret_cast<const uint4*>(svh + el * F);
 #pragma unroll
                         for (int j = 0; j < F / 2; ++j) {
                             const uint4 u = q[j];
@@ -664,23 +679,25 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
                     }
                 } else {
 #pragma unroll
-                    for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + cr.x];
+                    for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + el];
                 }
             };
             int k = 0;
             for (; k + 1 < n; k += 2) {  // two entries in flight, applied in list order
-                const int2 c0 = lst[32 * k], c1 = lst[32 * (k + 1)];
+                const int e0 = le[32 * k], e1 = le[32 * (k + 1)];
+                const float2 w0 = lw[32 * k], w1 = lw[32 * (k + 1)];
                 float4 v0[F], v1[F];
-                load(c0, v0);
-                load(c1, v1);
-                apply(c0, v0);
-                apply(c1, v1);
+                load(e0, v0);
+                load(e1, v1);
+                apply(w0, v0);
+                apply(w1, v1);
             }
             if (k < n) {
-                const int2 c0 = lst[32 * k];
+                const int e0 = le[32 * k];
+                const float2 w0 = lw[32 * k];
                 float4 v0[F];
-                load(c0, v0);
-                apply(c0, v0);
+                load(e0, v0);
+                apply(w0, v0);
             }
             // rows nyp + y (pol Y) sit nyp rows below rows y within every 64-column panel, with the
             // same swizzle phase (nyp is a multiple of 8)
@@ -690,11 +707,11 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             for (int fi = 0; fi < F; ++fi) {
                 if (fi >= nf) break;
                 uint8_t* t = tset + (size_t)fi * ba.tile_max;
-                *reinterpret_cast<__half*>(t + o_rx) = __float2half_rn(g[fi].x);
-                *reinterpret_cast<__half*>(t + o_ix) = __float2half_rn(g[fi].y);
+                *reinterpret_cast<uint32_t*>(t + o_rx) = pack_h2(g[fi].x, h1[fi].x);
+                *reinterpret_cast<uint32_t*>(t + o_ix) = pack_h2(g[fi].y, h1[fi].y);
                 if (P == 2) {
-                    *reinterpret_cast<__half*>(t + o_ry) = __float2half_rn(g[fi].z);
-                    *reinterpret_cast<__half*>(t + o_iy) = __float2half_rn(g[fi].w);
+                    *reinterpret_cast<uint32_t*>(t + o_ry) = pack_h2(g[fi].z, h1[fi].z);
+                    *reinterpret_cast<uint32_t*>(t + o_iy) = pack_h2(g[fi].w, h1[fi].w);
                 }
             }
         }
@@ -2604,67 +2621,86 @@ epic_status dftgemm_setup(epic_plan_s* p)
         if (gst == EPIC_OK) p->tc.grid_ps = true;
         else if (gst != EPIC_ERR_UNSUPPORTED) return gst;
     }
-    if (!cplx) {  // per-channel task lists of non-empty cells, longest list first
+    if (!cplx) {  // per-channel task lists of non-empty cell pairs, longest list first
         std::vector<int> coff, cptr, ce;
         std::vector<float2> cw;
         build_csr(p, coff, cptr, ce, cw);
-        // Cells of a channel sorted by contribution count (cells of equal count in Morton
-        // order, so that a warp's cells are near one another and share elements); groups of
-        // 32 consecutive cells (the lanes of one warp) store their (element, weight) entries
-        // interleaved, entry k of lane l at 32 k + l, padded with zero weights to the
-        // group's longest list, in the order order_warp_entries picks.
+        // A task is the cell pair (x, x + 1), x even, of one row of a channel's box; its
+        // entries are the elements that reach either cell (the union of the two cells'
+        // element-ordered lists) with both weights.  Pairs of a channel are sorted by entry
+        // count (equal counts in Morton order, so that a warp's pairs are near one another
+        // and share elements); groups of 32 consecutive pairs (the lanes of one warp) store
+        // their entries interleaved, entry k of lane l at 32 k + l, padded with zero
+        // weights to the group's longest list, in the order order_warp_entries picks.
         std::vector<int4> tasks;
-        std::vector<int2> ell;
+        std::vector<int> ell_e;
+        std::vector<float2> ell_w;
         std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
+        std::vector<float2> pw;  // weight pairs of the channel's pair lists
+        std::vector<int2> ord;
         bool fits = true;
         int tmax = 0, emax = 0;
         for (int c = 0; c < C && fits; ++c) {
             toff[c] = (int)tasks.size();
-            eoff[c] = (int)ell.size();
+            eoff[c] = (int)ell_e.size();
             const int* ptr = &cptr[coff[c]];
-            const int ncell = p->box[c].nx * p->box[c].ny;
+            const Box bx = p->box[c];
+            const int hp = bx.nx / 2;  // pairs per row (nx is a multiple of 8)
+            std::vector<std::vector<int2>> plist((size_t)hp * bx.ny);  // (element, 1 + index into pw)
+            pw.clear();
+            for (int y = 0; y < bx.ny; ++y)
+                for (int j = 0; j < hp; ++j) {
+                    const int r0 = y * bx.nx + 2 * j, r1 = r0 + 1;
+                    int a = ptr[r0], b = ptr[r1];
+                    std::vector<int2>& L = plist[(size_t)y * hp + j];
+                    while (a < ptr[r0 + 1] || b < ptr[r1 + 1]) {  // merge of two element-ordered lists
+                        const int ea = a < ptr[r0 + 1] ? ce[a] : INT32_MAX, eb = b < ptr[r1 + 1] ? ce[b] : INT32_MAX;
+                        const int el = std::min(ea, eb);
+                        const float w0 = ea == el ? cw[a++].x : 0.f, w1 = eb == el ? cw[b++].x : 0.f;
+                        pw.push_back(make_float2(w0, w1));
+                        L.push_back(make_int2(el, (int)pw.size()));
+                    }
+                }
             std::vector<int> idx;
-            for (int r = 0; r < ncell; ++r)
-                if (ptr[r + 1] > ptr[r]) idx.push_back(r);
-            const int bnx = p->box[c].nx;
-            auto morton = [bnx](int r) {
-                const unsigned x = (unsigned)(r % bnx), y = (unsigned)(r / bnx);
+            for (int q = 0; q < hp * bx.ny; ++q)
+                if (!plist[q].empty()) idx.push_back(q);
+            auto morton = [hp](int q) {
+                const unsigned x = (unsigned)(2 * (q % hp)), y = (unsigned)(q / hp);
                 unsigned m = 0;
                 for (int bit = 0; bit < 12; ++bit) m |= ((x >> bit) & 1u) << (2 * bit) | ((y >> bit) & 1u) << (2 * bit + 1);
                 return m;
             };
             std::stable_sort(idx.begin(), idx.end(), [&](int u, int v) {
-                const int nu = ptr[u + 1] - ptr[u], nv = ptr[v + 1] - ptr[v];
+                const size_t nu = plist[u].size(), nv = plist[v].size();
                 return nu != nv ? nu > nv : morton(u) < morton(v);
             });
+            const int n1 = p->P * bx.ny;
             for (size_t g0 = 0; g0 < idx.size(); g0 += 32) {
                 const int members = (int)std::min<size_t>(32, idx.size() - g0);
-                const int nmax = ptr[idx[g0] + 1] - ptr[idx[g0]];
-                const int base = (int)ell.size() - eoff[c];
+                const int nmax = (int)plist[idx[g0]].size();
+                const int base = (int)ell_e.size() - eoff[c];
                 if (nmax > 255) fits = false;
                 std::vector<std::vector<int2>> lists(members);
-                for (int l = 0; l < members; ++l) {
-                    const int r = idx[g0 + l];
-                    for (int k = ptr[r]; k < ptr[r + 1]; ++k)
-                        lists[l].push_back(make_int2(ce[k], __float_as_int_host(cw[k].x)));
+                for (int l = 0; l < members; ++l) lists[l] = plist[idx[g0 + l]];
+                ord.assign(32ull * nmax, make_int2(0, 0));
+                order_warp_entries(lists, nmax, ord.data());
+                for (const int2& en : ord) {
+                    ell_e.push_back(en.x);
+                    ell_w.push_back(en.y > 0 ? pw[en.y - 1] : make_float2(0.f, 0.f));
                 }
-                ell.resize(ell.size() + 32ull * nmax);
-                order_warp_entries(lists, nmax, ell.data() + (ell.size() - 32ull * nmax));
-                const Box bx = p->box[c];
-                const int n1 = p->P * bx.ny;
                 for (int l = 0; l < members; ++l) {
-                    const int r = idx[g0 + l];
-                    if (r >= (1 << 24)) fits = false;
-                    const int y = r / bx.nx, x = r - y * bx.nx;
-                    tasks.push_back(make_int4(r | (nmax << 24), base, (int)tile_half_off(y, x, n1),
+                    const int q = idx[g0 + l];
+                    if (q >= (1 << 24)) fits = false;
+                    const int y = q / hp, x = 2 * (q % hp);
+                    tasks.push_back(make_int4(q | (nmax << 24), base, (int)tile_half_off(y, x, n1),
                                               (int)tile_half_off(y, bx.nx + x, n1)));
                 }
             }
             tmax = std::max(tmax, (int)idx.size());
-            emax = std::max(emax, (int)ell.size() - eoff[c]);
+            emax = std::max(emax, (int)ell_e.size() - eoff[c]);
         }
         toff[C] = (int)tasks.size();
-        eoff[C] = (int)ell.size();
+        eoff[C] = (int)ell_e.size();
         if (fits && !tasks.empty()) {
             e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int4));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int4),
@@ -2672,8 +2708,11 @@ epic_status dftgemm_setup(epic_plan_s* p)
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gtask_off, toff.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask_off, toff.data(), toff.size() * sizeof(int),
                                                  cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell, ell.size() * sizeof(int2));
-            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell, ell.data(), ell.size() * sizeof(int2),
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_e, ell_e.size() * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_e, ell_e.data(), ell_e.size() * sizeof(int),
+                                                 cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_w, ell_w.size() * sizeof(float2));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_w, ell_w.data(), ell_w.size() * sizeof(float2),
                                                  cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_off, eoff.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_off, eoff.data(), eoff.size() * sizeof(int),
@@ -2690,11 +2729,13 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 p->tc.grid_variant = 1;
                 cudaFree(p->tc.gtask);
                 cudaFree(p->tc.gtask_off);
-                cudaFree(p->tc.gell);
+                cudaFree(p->tc.gell_e);
+                cudaFree(p->tc.gell_w);
                 cudaFree(p->tc.gell_off);
                 p->tc.gtask = nullptr;
                 p->tc.gtask_off = nullptr;
-                p->tc.gell = nullptr;
+                p->tc.gell_e = nullptr;
+                p->tc.gell_w = nullptr;
                 p->tc.gell_off = nullptr;
                 p->tc.gtask_max = 0;
                 if (p->tc.grid_ps) {
@@ -2702,7 +2743,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     if (kst != EPIC_OK) return kst;
                 }
             } else {
-                p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell.size() * sizeof(int2) +
+                p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell_e.size() * (sizeof(int) + sizeof(float2)) +
                                    (toff.size() + eoff.size()) * sizeof(int);
             }
         }
@@ -2831,7 +2872,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     ba.g = g;
                     ba.tasks = p->tc.gtask;
                     ba.task_off = p->tc.gtask_off;
-                    ba.ell = p->tc.gell;
+                    ba.ell_e = p->tc.gell_e;
+                    ba.ell_w = p->tc.gell_w;
                     ba.ell_off = p->tc.gell_off;
                     ba.max_tasks = p->tc.gtask_max;
                     ba.max_ell = p->tc.gell_max;

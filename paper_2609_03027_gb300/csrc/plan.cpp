@@ -171,10 +171,11 @@ void build_twiddles(int N, std::vector<float2>& tw)
     }
 }
 
-// Interleaves the (element, weight) entries of one warp's cells for the balanced
+// Interleaves the (element, payload) entries of one warp's tasks for the balanced
 // gridding kernel: entry k of lane l goes to out[32 k + l], every lane padded to nmax
-// entries with zero weights.  A cell's sum does not depend on the order of its
-// entries beyond FP32 rounding, so the order is chosen for the shared-memory gather:
+// entries with payload 0 (which the caller reads as zero weights).  A task's sums do
+// not depend on the order of its entries beyond FP32 rounding, so the order is chosen
+// for the shared-memory gather:
 // at step k the lanes of a warp read the 16-byte voltages of their k-th elements,
 // and 8 lanes that ask for different elements in the same 16-byte bank quad
 // (element mod 8) serialise.  Per step and per group of 8 lanes, lanes that must take
@@ -238,7 +239,7 @@ void order_warp_entries(const std::vector<std::vector<int2>>& cells, int nmax, i
                 out[32 * k + lanes[i]] = en;
                 r.erase(r.begin() + pick);
             }
-            const int2 zero = make_int2(first < 0 ? 0 : first, 0);  // weight +0.0f
+            const int2 zero = make_int2(first < 0 ? 0 : first, 0);
             for (int i = 0; i < nl; ++i)
                 if (pad[i]) out[32 * k + lanes[i]] = zero;
             for (int l = std::max(q0, members); l < q0 + 8; ++l) out[32 * k + l] = zero;
