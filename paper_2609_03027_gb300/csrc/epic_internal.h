@@ -59,7 +59,7 @@ struct TcState {
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list
     int* gell_e = nullptr;         // balanced gridding: interleaved entries, element
-    float2* gell_w = nullptr;      //   and (weight at x, weight at x + 1) of a cell pair
+    void* gell_w = nullptr;        //   and the weights of its run of cells (one per cell)
     int* gell_off = nullptr;       // [C + 1]
     int gell_max = 0;              // largest entry list (with padding)
     bool fast = false;             // TMEM-resident stage-2 operand, double-buffered stage 1 / B2

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "epic_internal.h"
 #include "kcommon.cuh"
@@ -458,32 +459,49 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
     }
 }
 
-// Balanced gridding kernel (real GCF weights).  A task is a pair of horizontally
-// adjacent cells (x even, x + 1) of a channel's box: its list holds every element
-// whose footprint covers either cell, with the two weights (one of them zero at a
-// footprint's edge), so each voltage read serves both cells and the two FP16 results
-// of a tile row leave as one 32-bit word.  Tasks are taken from a per-channel list
+// Balanced gridding kernel (real GCF weights).  A task is a run of kTaskCells
+// horizontally adjacent cells (x a multiple of kTaskCells) of a channel's box: its
+// list holds every element whose footprint covers any of them, with one weight per
+// cell (zero where the footprint ends), so each voltage read serves all the cells and
+// their FP16 results in a tile row leave as one 2 x kTaskCells-byte word.  Tasks are taken from a per-channel list
 // sorted by entry count, so the 32 lanes of a warp walk lists of nearly equal length
 // (a row-major walk keeps about 40% of the lanes busy), and the F frames of a pass are
 // assembled in shared-memory tiles that the TMA engine then stores with one bulk copy
 // per frame.  Tile buffers are double buffered across passes; cells no task touches
 // stay zero from the channel's first pass.  The entries of the 32 tasks a warp handles
 // together are interleaved (entry k of lane l at 32 k + l: elements as one 128-byte row,
-// weight pairs as one 256-byte row per step).  With H the unpacked voltages are held
+// weights as one 32 x 4 x kTaskCells-byte row per step).  With H the unpacked voltages are held
 // as FP16 pairs, the F frames of an element side by side (F x 8 bytes: X, Y of frame
 // 0, ...), so one 16-byte load per entry serves two frames; 4- and 8-bit samples are
 // exact in FP16, so the sums are bitwise those of the FP32 form (which polarisation
 // mixing uses).
+constexpr int kTaskCells = 2;                             // cells per gridding task (2 or 4; 4 measured no faster)
+using TaskW = std::conditional<kTaskCells == 4, float4, float2>::type;  // one weight per cell
+__host__ __device__ __forceinline__ void task_w_get(const float2& w, float* q) { q[0] = w.x; q[1] = w.y; }
+__host__ __device__ __forceinline__ void task_w_get(const float4& w, float* q)
+{
+    q[0] = w.x;
+    q[1] = w.y;
+    q[2] = w.z;
+    q[3] = w.w;
+}
+__host__ __device__ __forceinline__ void task_w_set(float2& w, const float* q) { w = make_float2(q[0], q[1]); }
+__host__ __device__ __forceinline__ void task_w_set(float4& w, const float* q) { w = make_float4(q[0], q[1], q[2], q[3]); }
+__device__ __forceinline__ void store_words(uint8_t* dst, const uint32_t (&w)[1]) { *reinterpret_cast<uint32_t*>(dst) = w[0]; }
+__device__ __forceinline__ void store_words(uint8_t* dst, const uint32_t (&w)[2])
+{
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+}
 constexpr int kGridBalThreads = 512;                      // gridding threads
 constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that issues the bulk copies
 
 struct GridBalArgs {
     GridArgs g;
-    const int4* tasks;      // per channel: (cell pair | group's longest list << 24, group's first
-                            //  entry, tile byte offsets of the pair's re X and im X words)
+    const int4* tasks;      // per channel: (cell run | group's longest list << 24, group's first
+                            //  entry, tile byte offsets of the run's re X and im X words)
     const int* task_off;    // [C + 1]
     const int* ell_e;       // per channel: element of each entry, 32 lanes interleaved per group
-    const float2* ell_w;    // per channel: (weight at x, weight at x + 1) of each entry
+    const TaskW* ell_w;     // per channel: weights at x, x + 1, ... of each entry
     const int* ell_off;     // [C + 1]
     int max_tasks;          // largest task count of a channel
     int max_ell;            // largest entry count of a channel (with padding)
@@ -497,7 +515,7 @@ __host__ __device__ inline size_t grid_bal_smem(int F, int A, int frame_bytes, i
     size_t b = 2ull * F * ap + 16ull * F * A;  // raw voltages, unpacked voltages
     b = (b + 127) & ~(size_t)127;
     b += 2ull * F * tile_max;                  // tile buffers
-    b += 16ull * max_tasks + 12ull * max_list;  // task list, entries (weight pairs, elements)
+    b += 16ull * max_tasks + (4ull + sizeof(TaskW)) * max_list;  // task list, entries (weights, elements)
     return b;
 }
 
@@ -526,7 +544,7 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
     const size_t tiles_at = ((size_t)2 * F * APr + 16ull * F * A + 127) & ~(size_t)127;
     uint8_t* stile = gsm + tiles_at;                                   // [2][F][tile_max]
     int4* stask = reinterpret_cast<int4*>(stile + 2ull * F * ba.tile_max);
-    float2* sell_w = reinterpret_cast<float2*>(stask + ba.max_tasks);
+    TaskW* sell_w = reinterpret_cast<TaskW*>(stask + ba.max_tasks);
     int* sell_e = reinterpret_cast<int*>(sell_w + ba.max_ell);
 
     const long long W = (long long)a.n_ch * a.nt;
@@ -636,26 +654,25 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
         for (int s = tid; s < ntask && tid < nthr; s += nthr) {
             const int4 tk = stask[s];
             const int n = (int)((unsigned)tk.x >> 24);
-            float4 g[F], h1[F];  // cells x and x + 1
+            float4 g[kTaskCells][F];  // cells x, x + 1, ...
 #pragma unroll
-            for (int fi = 0; fi < F; ++fi) {
-                g[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
-                h1[fi] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int q = 0; q < kTaskCells; ++q)
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) g[q][fi] = make_float4(0.f, 0.f, 0.f, 0.f);
             const int* le = sell_e + tk.y + (s & 31);
-            const float2* lw = sell_w + tk.y + (s & 31);
-            auto apply = [&](float2 w, const float4 (&v)[F]) {
+            const TaskW* lw = sell_w + tk.y + (s & 31);
+            auto apply = [&](TaskW w, const float4 (&v)[F]) {
+                float wq[kTaskCells];
+                task_w_get(w, wq);
 #pragma unroll
-                for (int fi = 0; fi < F; ++fi) {
-                    g[fi].x = fmaf(w.x, v[fi].x, g[fi].x);
-                    g[fi].y = fmaf(w.x, v[fi].y, g[fi].y);
-                    g[fi].z = fmaf(w.x, v[fi].z, g[fi].z);
-                    g[fi].w = fmaf(w.x, v[fi].w, g[fi].w);
-                    h1[fi].x = fmaf(w.y, v[fi].x, h1[fi].x);
-                    h1[fi].y = fmaf(w.y, v[fi].y, h1[fi].y);
-                    h1[fi].z = fmaf(w.y, v[fi].z, h1[fi].z);
-                    h1[fi].w = fmaf(w.y, v[fi].w, h1[fi].w);
-                }
+                for (int q = 0; q < kTaskCells; ++q)
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) {
+                        g[q][fi].x = fmaf(wq[q], v[fi].x, g[q][fi].x);
+                        g[q][fi].y = fmaf(wq[q], v[fi].y, g[q][fi].y);
+                        g[q][fi].z = fmaf(wq[q], v[fi].z, g[q][fi].z);
+                        g[q][fi].w = fmaf(wq[q], v[fi].w, g[q][fi].w);
+                    }
             };
             auto load = [&](int el, float4 (&v)[F]) {  // frames past nf read stale but valid entries
                 if constexpr (H) {
@@ -685,7 +702,7 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             int k = 0;
             for (; k + 1 < n; k += 2) {  // two entries in flight, applied in list order
                 const int e0 = le[32 * k], e1 = le[32 * (k + 1)];
-                const float2 w0 = lw[32 * k], w1 = lw[32 * (k + 1)];
+                const TaskW w0 = lw[32 * k], w1 = lw[32 * (k + 1)];
                 float4 v0[F], v1[F];
                 load(e0, v0);
                 load(e1, v1);
@@ -694,7 +711,7 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             }
             if (k < n) {
                 const int e0 = le[32 * k];
-                const float2 w0 = lw[32 * k];
+                const TaskW w0 = lw[32 * k];
                 float4 v0[F];
                 load(e0, v0);
                 apply(w0, v0);
@@ -707,11 +724,19 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             for (int fi = 0; fi < F; ++fi) {
                 if (fi >= nf) break;
                 uint8_t* t = tset + (size_t)fi * ba.tile_max;
-                *reinterpret_cast<uint32_t*>(t + o_rx) = pack_h2(g[fi].x, h1[fi].x);
-                *reinterpret_cast<uint32_t*>(t + o_ix) = pack_h2(g[fi].y, h1[fi].y);
+                uint32_t rx[kTaskCells / 2], ix[kTaskCells / 2], ry[kTaskCells / 2], iy[kTaskCells / 2];
+#pragma unroll
+                for (int q = 0; q < kTaskCells / 2; ++q) {
+                    rx[q] = pack_h2(g[2 * q][fi].x, g[2 * q + 1][fi].x);
+                    ix[q] = pack_h2(g[2 * q][fi].y, g[2 * q + 1][fi].y);
+                    ry[q] = pack_h2(g[2 * q][fi].z, g[2 * q + 1][fi].z);
+                    iy[q] = pack_h2(g[2 * q][fi].w, g[2 * q + 1][fi].w);
+                }
+                store_words(t + o_rx, rx);
+                store_words(t + o_ix, ix);
                 if (P == 2) {
-                    *reinterpret_cast<uint32_t*>(t + o_ry) = pack_h2(g[fi].z, h1[fi].z);
-                    *reinterpret_cast<uint32_t*>(t + o_iy) = pack_h2(g[fi].w, h1[fi].w);
+                    store_words(t + o_ry, ry);
+                    store_words(t + o_iy, iy);
                 }
             }
         }
@@ -2625,18 +2650,19 @@ epic_status dftgemm_setup(epic_plan_s* p)
         std::vector<int> coff, cptr, ce;
         std::vector<float2> cw;
         build_csr(p, coff, cptr, ce, cw);
-        // A task is the cell pair (x, x + 1), x even, of one row of a channel's box; its
-        // entries are the elements that reach either cell (the union of the two cells'
-        // element-ordered lists) with both weights.  Pairs of a channel are sorted by entry
-        // count (equal counts in Morton order, so that a warp's pairs are near one another
-        // and share elements); groups of 32 consecutive pairs (the lanes of one warp) store
-        // their entries interleaved, entry k of lane l at 32 k + l, padded with zero
-        // weights to the group's longest list, in the order order_warp_entries picks.
+        // A task is the run of kTaskCells cells (x, x + 1, ...), x a multiple of kTaskCells,
+        // of one row of a channel's box; its entries are the elements that reach any of them
+        // (the union of the cells' element-ordered lists) with one weight per cell.  Runs of
+        // a channel are sorted by entry count (equal counts in Morton order, so that a warp's
+        // runs are near one another and share elements); groups of 32 consecutive runs (the
+        // lanes of one warp) store their entries interleaved, entry k of lane l at 32 k + l,
+        // padded with zero weights to the group's longest list, in the order
+        // order_warp_entries picks.
         std::vector<int4> tasks;
         std::vector<int> ell_e;
-        std::vector<float2> ell_w;
+        std::vector<TaskW> ell_w;
         std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
-        std::vector<float2> pw;  // weight pairs of the channel's pair lists
+        std::vector<TaskW> pw;  // weights of the channel's run lists
         std::vector<int2> ord;
         bool fits = true;
         int tmax = 0, emax = 0;
@@ -2645,19 +2671,26 @@ epic_status dftgemm_setup(epic_plan_s* p)
             eoff[c] = (int)ell_e.size();
             const int* ptr = &cptr[coff[c]];
             const Box bx = p->box[c];
-            const int hp = bx.nx / 2;  // pairs per row (nx is a multiple of 8)
+            const int hp = bx.nx / kTaskCells;  // runs per row (nx is a multiple of 8)
             std::vector<std::vector<int2>> plist((size_t)hp * bx.ny);  // (element, 1 + index into pw)
             pw.clear();
             for (int y = 0; y < bx.ny; ++y)
                 for (int j = 0; j < hp; ++j) {
-                    const int r0 = y * bx.nx + 2 * j, r1 = r0 + 1;
-                    int a = ptr[r0], b = ptr[r1];
+                    const int r0 = y * bx.nx + kTaskCells * j;
+                    int at[kTaskCells];
+                    for (int q = 0; q < kTaskCells; ++q) at[q] = ptr[r0 + q];
                     std::vector<int2>& L = plist[(size_t)y * hp + j];
-                    while (a < ptr[r0 + 1] || b < ptr[r1 + 1]) {  // merge of two element-ordered lists
-                        const int ea = a < ptr[r0 + 1] ? ce[a] : INT32_MAX, eb = b < ptr[r1 + 1] ? ce[b] : INT32_MAX;
-                        const int el = std::min(ea, eb);
-                        const float w0 = ea == el ? cw[a++].x : 0.f, w1 = eb == el ? cw[b++].x : 0.f;
-                        pw.push_back(make_float2(w0, w1));
+                    for (;;) {  // merge of the cells' element-ordered lists
+                        int el = INT32_MAX;
+                        for (int q = 0; q < kTaskCells; ++q)
+                            if (at[q] < ptr[r0 + q + 1]) el = std::min(el, ce[at[q]]);
+                        if (el == INT32_MAX) break;
+                        float wq[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int q = 0; q < kTaskCells; ++q)
+                            if (at[q] < ptr[r0 + q + 1] && ce[at[q]] == el) wq[q] = cw[at[q]++].x;
+                        TaskW w;
+                        task_w_set(w, wq);
+                        pw.push_back(w);
                         L.push_back(make_int2(el, (int)pw.size()));
                     }
                 }
@@ -2665,7 +2698,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
             for (int q = 0; q < hp * bx.ny; ++q)
                 if (!plist[q].empty()) idx.push_back(q);
             auto morton = [hp](int q) {
-                const unsigned x = (unsigned)(2 * (q % hp)), y = (unsigned)(q / hp);
+                const unsigned x = (unsigned)(kTaskCells * (q % hp)), y = (unsigned)(q / hp);
                 unsigned m = 0;
                 for (int bit = 0; bit < 12; ++bit) m |= ((x >> bit) & 1u) << (2 * bit) | ((y >> bit) & 1u) << (2 * bit + 1);
                 return m;
@@ -2686,12 +2719,12 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 order_warp_entries(lists, nmax, ord.data());
                 for (const int2& en : ord) {
                     ell_e.push_back(en.x);
-                    ell_w.push_back(en.y > 0 ? pw[en.y - 1] : make_float2(0.f, 0.f));
+                    ell_w.push_back(en.y > 0 ? pw[en.y - 1] : TaskW{});
                 }
                 for (int l = 0; l < members; ++l) {
                     const int q = idx[g0 + l];
                     if (q >= (1 << 24)) fits = false;
-                    const int y = q / hp, x = 2 * (q % hp);
+                    const int y = q / hp, x = kTaskCells * (q % hp);
                     tasks.push_back(make_int4(q | (nmax << 24), base, (int)tile_half_off(y, x, n1),
                                               (int)tile_half_off(y, bx.nx + x, n1)));
                 }
@@ -2711,8 +2744,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_e, ell_e.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_e, ell_e.data(), ell_e.size() * sizeof(int),
                                                  cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_w, ell_w.size() * sizeof(float2));
-            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_w, ell_w.data(), ell_w.size() * sizeof(float2),
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_w, ell_w.size() * sizeof(TaskW));
+            if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_w, ell_w.data(), ell_w.size() * sizeof(TaskW),
                                                  cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMalloc(&p->tc.gell_off, eoff.size() * sizeof(int));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gell_off, eoff.data(), eoff.size() * sizeof(int),
@@ -2743,7 +2776,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     if (kst != EPIC_OK) return kst;
                 }
             } else {
-                p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell_e.size() * (sizeof(int) + sizeof(float2)) +
+                p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell_e.size() * (sizeof(int) + sizeof(TaskW)) +
                                    (toff.size() + eoff.size()) * sizeof(int);
             }
         }
@@ -2873,7 +2906,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     ba.tasks = p->tc.gtask;
                     ba.task_off = p->tc.gtask_off;
                     ba.ell_e = p->tc.gell_e;
-                    ba.ell_w = p->tc.gell_w;
+                    ba.ell_w = reinterpret_cast<const TaskW*>(p->tc.gell_w);
                     ba.ell_off = p->tc.gell_off;
                     ba.max_tasks = p->tc.gtask_max;
                     ba.max_ell = p->tc.gell_max;

@@ -64,7 +64,9 @@ def test_tuner_keeps_parity_and_reports_params(path):
         for name, val in rep["params"].items():
             assert plan.get_param(name) == val
         after = plan.image(v).cpu().numpy()
-    assert rel_errors(after, before.astype(np.float64)).max() <= 1e-6
+    # FP32 summation order only; on the tensor path the two gridding kernels sum a cell in
+    # different orders, which can flip the rounding of an FP16 grid value
+    assert rel_errors(after, before.astype(np.float64)).max() <= (1e-5 if path == "dftgemm" else 1e-6)
     assert_parity(after, oracle_image(cfg, vn), path, "after tuning")
 
 
