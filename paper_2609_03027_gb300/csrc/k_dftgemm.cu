@@ -498,7 +498,8 @@ constexpr int kGridBalBlock = kGridBalThreads + 32;        // + one warp that is
 struct GridBalArgs {
     GridArgs g;
     const int4* tasks;      // per channel: (cell run | group's longest list << 24, group's first
-                            //  entry, tile byte offsets of the run's re X and im X words)
+                            //  entry, tile byte offsets of the run's re X and im X words, or -1
+                            //  for a padding task); warp w takes groups w, w + 16, ... of 32 tasks
     const int* task_off;    // [C + 1]
     const int* ell_e;       // per channel: element of each entry, 32 lanes interleaved per group
     const TaskW* ell_w;     // per channel: weights at x, x + 1, ... of each entry
@@ -722,7 +723,7 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
             const uint32_t o_ry = o_rx + (uint32_t)nyp * 128, o_iy = o_ix + (uint32_t)nyp * 128;
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) {
-                if (fi >= nf) break;
+                if (fi >= nf || tk.z < 0) break;  // tk.z < 0: padding task
                 uint8_t* t = tset + (size_t)fi * ba.tile_max;
                 uint32_t rx[kTaskCells / 2], ix[kTaskCells / 2], ry[kTaskCells / 2], iy[kTaskCells / 2];
 #pragma unroll
@@ -2708,6 +2709,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 return nu != nv ? nu > nv : morton(u) < morton(v);
             });
             const int n1 = p->P * bx.ny;
+            std::vector<std::vector<int4>> gtasks;  // the 32 tasks of each group (padding tasks: no store)
+            std::vector<int> gcost;
             for (size_t g0 = 0; g0 < idx.size(); g0 += 32) {
                 const int members = (int)std::min<size_t>(32, idx.size() - g0);
                 const int nmax = (int)plist[idx[g0]].size();
@@ -2721,15 +2724,40 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     ell_e.push_back(en.x);
                     ell_w.push_back(en.y > 0 ? pw[en.y - 1] : TaskW{});
                 }
+                std::vector<int4> gt(32, make_int4(nmax << 24, base, -1, -1));
                 for (int l = 0; l < members; ++l) {
                     const int q = idx[g0 + l];
                     if (q >= (1 << 24)) fits = false;
                     const int y = q / hp, x = kTaskCells * (q % hp);
-                    tasks.push_back(make_int4(q | (nmax << 24), base, (int)tile_half_off(y, x, n1),
-                                              (int)tile_half_off(y, bx.nx + x, n1)));
+                    gt[l] = make_int4(q | (nmax << 24), base, (int)tile_half_off(y, x, n1),
+                                      (int)tile_half_off(y, bx.nx + x, n1));
                 }
+                gtasks.push_back(gt);
+                gcost.push_back(nmax + 1);  // list steps + the tile stores
             }
-            tmax = std::max(tmax, (int)idx.size());
+            // Warp w of the kernel takes groups w, w + W, w + 2 W, ... of the task list (W
+            // gridding warps) and a pass ends when its slowest warp does, so the groups are
+            // dealt out longest first to the least-loaded warp and laid out in that order;
+            // positions a warp does not use hold groups of padding tasks (no entries, no store).
+            const int W = kGridBalThreads / 32;
+            std::vector<std::vector<int>> wl(W);
+            std::vector<long long> load(W, 0);
+            for (int g = 0; g < (int)gtasks.size(); ++g) {  // groups are in decreasing cost order
+                int w = 0;
+                for (int v = 1; v < W; ++v)
+                    if (load[v] < load[w]) w = v;
+                wl[w].push_back(g);
+                load[w] += gcost[g];
+            }
+            size_t rounds = 0;
+            for (const auto& l : wl) rounds = std::max(rounds, l.size());
+            const std::vector<int4> pad(32, make_int4(0, 0, -1, -1));
+            for (size_t j = 0; j < rounds; ++j)
+                for (int w = 0; w < W; ++w) {
+                    const std::vector<int4>& gt = j < wl[w].size() ? gtasks[wl[w][j]] : pad;
+                    tasks.insert(tasks.end(), gt.begin(), gt.end());
+                }
+            tmax = std::max(tmax, (int)(tasks.size() - toff[c]));
             emax = std::max(emax, (int)ell_e.size() - eoff[c]);
         }
         toff[C] = (int)tasks.size();
