@@ -135,6 +135,13 @@ typedef struct {
     int input_bits;         /* 4 or 8                                                             */
     int sub_int;            /* samples per image set, 0 = the whole block                         */
     int pol_mix;            /* 1 when the plan has a polarisation-mixing kernel (jones)           */
+    int tc_kernel;          /* DFT-as-GEMM path: transform kernel of a call -- 3 the warp-
+                               specialised control-warpgroup kernel, 1 / 2 its older warp-
+                               specialised forms, 4 / 5 the 32-column-slab fallbacks; 0 for the
+                               FFT paths                                                          */
+    int row_parts;          /* DFT-as-GEMM path: most row parts of a channel's occupied grid (tall
+                               grids are transformed in parts of rows whose stage-2 sums add up);
+                               1 when every channel is one part; 0 for the FFT paths              */
 } epic_plan_info;
 
 /* flags of epic_image / epic_image_host */

@@ -64,6 +64,7 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.gell_e);
     cudaFree(p->tc.gell_w);
     cudaFree(p->tc.gell_off);
+    cudaFree(p->tc.tbox);
     cudaFree(p->scratch);
     cudaFree(p->stage_volt);
     cudaFree(p->stage_out);
@@ -358,6 +359,12 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
     info->input_bits = p->bits;
     info->sub_int = p->sub;
     info->pol_mix = p->jones.empty() ? 0 : 1;
+    info->tc_kernel = 0;
+    info->row_parts = 0;
+    if (p->path == EPIC_PATH_DFTGEMM_FP16) {
+        info->tc_kernel = p->tc.ws ? p->tc.ws_variant : p->tc.fast ? 4 : 5;
+        for (const int4& r : p->tc.tbox_h) info->row_parts = std::max(info->row_parts, r.y);
+    }
     return EPIC_OK;
 }
 

@@ -75,6 +75,13 @@ struct TcState {
     float* partial = nullptr;      // k_dftgemm_ws3: partial sums of items split between blocks
     int* counters = nullptr;       // k_dftgemm_ws3: per item, parts stored so far
     int split = -1;                // k_dftgemm_ws3 work split: -1 auto, 0 whole items, 1 equal shares
+    // Row parts of k_dftgemm_ws3: channel c's box rows are cut into H parts of nyh rows
+    // (padded to H * nyh rows, the extra rows zero); each part is a grid tile of its own
+    // (P * nyh rows) and a stage-1 / stage-2 step of its own, so tall boxes fit in TMEM.
+    std::vector<int4> tbox_h;      // [C] (nyh, H, H * nyh, 0) on the host
+    int4* tbox = nullptr;          // same, on the device (every tensor-path plan)
+    bool parts = false;            // some channel has H > 1 (only k_dftgemm_ws3 takes it)
+    int nbt = 2;                   // k_dftgemm_ws3: tile-part buffers in shared memory (2..4)
 };
 
 struct KernelEvent {

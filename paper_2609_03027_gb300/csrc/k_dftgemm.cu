@@ -82,6 +82,20 @@ __host__ __device__ inline int pad64(int k) { return (k + 63) & ~63; }
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Row parts of a box of `rows` rows (a multiple of 8 for two pols, 16 for one) for
+// k_dftgemm_ws3 with D1 slots of D TMEM columns: the fewest parts H whose equal height
+// nyh (rounded up to that multiple) gives P * nyh <= D.  Returns (nyh, H, H * nyh, 0),
+// or H = 0 when no height fits.
+inline int4 row_parts(int rows, int P, int D)
+{
+    const int q = P == 2 ? 8 : 16;
+    for (int H = 1; H <= rows / q; ++H) {
+        const int nyh = ((rows + H - 1) / H + q - 1) / q * q;
+        if (P * nyh <= D) return make_int4(nyh, H, H * nyh, 0);
+    }
+    return make_int4(0, 0, 0, 0);
+}
+
 inline int __float_as_int_host(float f)
 {
     int i;
@@ -117,6 +131,8 @@ struct MmaArgs {
     int sub;                    // k_dftgemm_ws3<2>: samples per image set
     int iv0;                    // k_dftgemm_ws3<2>: image set of the chunk's first sample
     int C;                      // channels of the plan (image sets are [C][nprod][N][N])
+    const int4* tbox;           // k_dftgemm_ws3: per channel row parts (nyh, H, H nyh, 0)
+    int nbt;                    // k_dftgemm_ws3: tile-part buffers in shared memory (2..4)
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -172,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                                                            const int* __restrict__ ce,
                                                            const float2* __restrict__ cw,
                                                            const float4* __restrict__ jones,
+                                                           const int4* __restrict__ tbox,
                                                            uint8_t* __restrict__ tiles,
                                                            unsigned long long tile_stride)
 {
@@ -180,7 +197,10 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
     const int cl = blockIdx.y, c = c0 + cl;
     const float4* jm = jones ? jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
     const int4 b = box[c];
-    const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
+    const int nxp = b.z, nyp = b.w, ncell = nxp * nyp;
+    const int4 tp = tbox[c];  // row parts: rows nyp .. H nyh - 1 are written as zeros
+    const int nyh = tp.x, N1h = P * nyh;
+    const uint32_t part_bytes = (uint32_t)N1h * pad64(2 * nxp) * 2;
     const int* gptr = cell_ptr + cell_off[c];
     const int* ptr = gptr;
     int2* con = nullptr;
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
     }
     const int f0 = blockIdx.x * fpc, f1 = min(nt, f0 + fpc);
     const int half = nxp >> 1;
-    const int tasks = nyp * half;
+    const int tasks = tp.z * half;
     for (int tb = f0; tb < f1; tb += F) {
         const int nf = min(F, f1 - tb);
         __syncthreads();
@@ -214,8 +234,8 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
 #pragma unroll
                 for (int f = 0; f < F; ++f) g[j][f] = make_float4(0.f, 0.f, 0.f, 0.f);
                 const int r = y * nxp + x + j;
-                const int q1 = ptr[r + 1];
-                for (int q = ptr[r]; q < q1; ++q) {
+                const int q1 = y < nyp ? ptr[r + 1] : 0;
+                for (int q = y < nyp ? ptr[r] : 0; q < q1; ++q) {
                     int e;
                     float2 w;
                     if (CSR_SMEM) {
@@ -242,19 +262,20 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid(const uint8_t* __rest
                     }
                 }
             }
-            // cells (y, x) and (y, x+1): K index x (re) and nxp + x (im), rows p*nyp + y
+            // cells (y, x) and (y, x+1): K index x (re) and nxp + x (im), in row part y / nyh at
+            // rows p*nyh + y % nyh
             const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
+            const int hpart = y / nyh, R0 = y - hpart * nyh;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nf) break;
-                uint8_t* tile = tiles + ((size_t)(tb + f) * n_ch + cl) * tile_stride;
-                const int R0 = y;
-                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_re, N1) + within) = pack_h2(g[0][f].x, g[1][f].x);
-                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_im, N1) + within) = pack_h2(g[0][f].y, g[1][f].y);
+                uint8_t* tile = tiles + ((size_t)(tb + f) * n_ch + cl) * tile_stride + (size_t)hpart * part_bytes;
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_re, N1h) + within) = pack_h2(g[0][f].x, g[1][f].x);
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_im, N1h) + within) = pack_h2(g[0][f].y, g[1][f].y);
                 if (P == 2) {
-                    const int R1 = nyp + y;
-                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1) + within) = pack_h2(g[0][f].z, g[1][f].z);
-                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1) + within) = pack_h2(g[0][f].w, g[1][f].w);
+                    const int R1 = nyh + R0;
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1h) + within) = pack_h2(g[0][f].z, g[1][f].z);
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1h) + within) = pack_h2(g[0][f].w, g[1][f].w);
                 }
             }
         }
@@ -286,6 +307,7 @@ struct GridArgs {
     int bulk;       // 1: voltage frames copied by the TMA engine (frame bytes % 16 == 0, 16-byte aligned base)
     int bits;       // 4: 4+4-bit bytes, 8: 8+8-bit sample pairs
     const float4* jones;  // [C][A][2] polarisation-mixing rows (conj J), or nullptr
+    const int4* tbox;     // [C] row parts of the tiles: (nyh, H, H nyh, 0)
 };
 
 __host__ __device__ inline size_t grid_ps_smem(int F, int A, int frame_bytes, int max_cells, int max_list, bool cplx)
@@ -346,7 +368,10 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
         const long long wn = w + nf;
         const int c = a.c0 + cl;
         const int4 b = a.box[c];
-        const int nxp = b.z, nyp = b.w, N1 = P * nyp, ncell = nxp * nyp;
+        const int nxp = b.z, nyp = b.w, ncell = nxp * nyp;
+        const int4 tp = a.tbox[c];  // row parts: rows nyp .. H nyh - 1 are written as zeros
+        const int nyh = tp.x, N1h = P * nyh;
+        const uint32_t part_bytes = (uint32_t)N1h * pad64(2 * nxp) * 2;
         const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         if (a.bulk && tid == 0 && wn < w1) {  // the other buffer was consumed by the previous pass
             fetch(wn, buf ^ 1);
@@ -392,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
         }
         __syncthreads();
         const int half = nxp >> 1;
-        const int tasks = nyp * half;
+        const int tasks = tp.z * half;
         for (int task = tid; task < tasks; task += blockDim.x) {
             const int y = task / half, x = 2 * (task - y * half);
             float4 g[2][F];
@@ -401,8 +426,8 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) g[j][fi] = make_float4(0.f, 0.f, 0.f, 0.f);
                 const int r = y * nxp + x + j;
-                const int q1 = sptr[r + 1];
-                for (int q = sptr[r]; q < q1; ++q) {
+                const int q1 = y < nyp ? sptr[r + 1] : 0;
+                for (int q = y < nyp ? sptr[r] : 0; q < q1; ++q) {
                     int e;
                     float2 wv;
                     if (CPLX) {
@@ -432,17 +457,19 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
                 }
             }
             const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
+            const int hpart = y / nyh, R0 = y - hpart * nyh;
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) {
                 if (fi >= nf) break;
-                uint8_t* tile = a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride;
-                *reinterpret_cast<uint32_t*>(tile + sw_chunk(y, kc_re, N1) + within) = pack_h2(g[0][fi].x, g[1][fi].x);
-                *reinterpret_cast<uint32_t*>(tile + sw_chunk(y, kc_im, N1) + within) = pack_h2(g[0][fi].y, g[1][fi].y);
+                uint8_t* tile =
+                    a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride + (size_t)hpart * part_bytes;
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_re, N1h) + within) = pack_h2(g[0][fi].x, g[1][fi].x);
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_im, N1h) + within) = pack_h2(g[0][fi].y, g[1][fi].y);
                 if (P == 2) {
-                    const int R1 = nyp + y;
-                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1) + within) =
+                    const int R1 = nyh + R0;
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1h) + within) =
                         pack_h2(g[0][fi].z, g[1][fi].z);
-                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1) + within) =
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1h) + within) =
                         pack_h2(g[0][fi].w, g[1][fi].w);
                 }
             }
@@ -525,6 +552,16 @@ __host__ __device__ __forceinline__ uint32_t tile_half_off(int R, int k, int N1)
     return (uint32_t)((k >> 6) * (N1 * 128) + R * 128 + ((((k >> 3) & 7) ^ (R & 7)) << 4) + ((k & 7) << 1));
 }
 
+// Byte offset of the FP16 at (pol-X row y, K index k) of a grid tile cut into row parts of
+// nyh rows: part h = y / nyh is an operand of its own (P nyh rows: pol X rows 0..nyh-1, pol
+// Y rows nyh..2 nyh-1, so a pol-Y value sits nyh * 128 bytes after its pol-X value),
+// part_bytes apart.  One part (nyh = box rows) is the plain layout.
+__host__ __device__ __forceinline__ uint32_t tile_part_off(int y, int k, int nyh, int P, uint32_t part_bytes)
+{
+    const int h = y / nyh;
+    return (uint32_t)h * part_bytes + tile_half_off(y - h * nyh, k, P * nyh);
+}
+
 template <int F, bool H>
 __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalArgs ba)
 {
@@ -590,14 +627,16 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
         d_nf = 0;
     };
     int4 b = make_int4(0, 0, 0, 0);  // box of the staged channel (read once per channel, not per pass)
+    int4 tp = make_int4(0, 0, 0, 0);  // and its row parts
     for (long long w = w0; w < w1;) {
         const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
         const long long wn = w + nf;
         const int c = a.c0 + cl;
         if (cl != staged) b = a.box[c];
-        const int nxp = b.z, nyp = b.w, N1 = P * nyp;
+        if (cl != staged) tp = a.tbox[c];
+        const int nxp = b.z, nyh = tp.x;
         const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
-        const uint32_t tile_bytes = (uint32_t)N1 * pad64(2 * nxp) * 2;
+        const uint32_t tile_bytes = (uint32_t)(P * tp.z) * pad64(2 * nxp) * 2;  // every part
         if (cl != staged) {  // new channel: zeroed tile buffers, its task list and entries
             if (tma) {
                 store_deferred();
@@ -717,10 +756,10 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
                 load(e0, v0);
                 apply(w0, v0);
             }
-            // rows nyp + y (pol Y) sit nyp rows below rows y within every 64-column panel, with the
-            // same swizzle phase (nyp is a multiple of 8)
+            // pol-Y rows sit nyh rows below the pol-X rows of their part within every 64-column
+            // panel, with the same swizzle phase (nyh is a multiple of 8)
             const uint32_t o_rx = (uint32_t)tk.z, o_ix = (uint32_t)tk.w;
-            const uint32_t o_ry = o_rx + (uint32_t)nyp * 128, o_iy = o_ix + (uint32_t)nyp * 128;
+            const uint32_t o_ry = o_rx + (uint32_t)nyh * 128, o_iy = o_ix + (uint32_t)nyh * 128;
 #pragma unroll
             for (int fi = 0; fi < F; ++fi) {
                 if (fi >= nf || tk.z < 0) break;  // tk.z < 0: padding task
@@ -870,11 +909,11 @@ __device__ __forceinline__ void chain_ss(uint32_t d, uint64_t da, uint64_t db, u
 }
 
 template <int KS>
-__device__ __forceinline__ void chain_ts(uint32_t d, uint32_t at, uint64_t db, uint32_t pb16, uint32_t id)
+__device__ __forceinline__ void chain_ts(uint32_t d, uint32_t at, uint64_t db, uint32_t pb16, uint32_t id, bool acc)
 {
 #pragma unroll
     for (int k = 0; k < KS; ++k)
-        tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb16 + (k & 3) * 2), id, k > 0);
+        tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb16 + (k & 3) * 2), id, acc || k > 0);
 }
 
 #define EPIC_KS_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
@@ -897,20 +936,21 @@ __device__ __forceinline__ void issue_ss(int ks, uint32_t d, uint32_t sa, uint32
     }
 }
 
-// A in TMEM (K halves packed in pairs: 8 columns per K step), B in shared memory
+// A in TMEM (K halves packed in pairs: 8 columns per K step), B in shared memory; with
+// acc the chain adds to what D holds (a later row part of the same stage-2 sum)
 __device__ __forceinline__ void issue_ts(int ks, uint32_t d, uint32_t at, uint32_t sb, uint32_t b_panel_bytes,
-                                         uint32_t id)
+                                         uint32_t id, bool acc = false)
 {
     const uint64_t db = tc::smem_desc_sw128(sb);
     const uint32_t pb = b_panel_bytes >> 4;
     switch (ks) {
 #define EPIC_TS(n) \
-    case n: chain_ts<n>(d, at, db, pb, id); break;
+    case n: chain_ts<n>(d, at, db, pb, id, acc); break;
         EPIC_KS_CASES(EPIC_TS)
 #undef EPIC_TS
         default:
             for (int k = 0; k < ks; ++k)
-                tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb + (k & 3) * 2), id, k > 0);
+                tc::mma_f16_ta(d, at + 8 * k, db + (uint64_t)((k >> 2) * pb + (k & 3) * 2), id, acc || k > 0);
     }
 }
 
@@ -1892,15 +1932,23 @@ __global__ void __launch_bounds__(kWs2Threads, 1) k_dftgemm_ws2(MmaArgs a)
 // Third warp-specialised kernel: 16 epilogue warps and a control warpgroup in
 // separate register budgets (setmaxnreg), so that the threads issuing the MMAs and
 // tile copies -- blocking while the tensor pipe is busy -- hold up no epilogue warp.
-// Work item, operands and TMEM layout as k_dftgemm_ws2:
-//   stage-1 issuer (warp 17, lane 0), per frame t:
-//     wait d1_full(t) -> copy tile t+2 into the buffer S1(t) read (tile t+10 -> L2);
-//     wait b2_full(t) and tile t+2 -> S1(t+2) -> d1_full[t&1]
-//   stage-2 issuer (warp 16, lane 0), per frame t:
-//     wait b2_full(t) [and d2_empty(t-1)] -> S2(t) -> d2_full
-//   epilogue warps 0-15, per frame t:
-//     wait d1_full(t) -> epilogue 1 (t) -> arrive b2_full[t&1];
-//     wait d2_full(t-1) -> epilogue 2 (t-1) -> arrive d2_empty
+// Work item, operands and TMEM layout as k_dftgemm_ws2, except that a channel's box rows
+// may come in H row parts (tall boxes): stage 2 sums over the box rows, so part h of frame t
+// is a step of its own -- its tile part through stage 1 (D1 of P nyh columns), epilogue 1 and
+// a stage-2 chain over its K range that adds to D2 (h > 0) -- and D2 holds the frame once
+// its last part is in.  Sub-frame u = t H + h; NB (2..4) tile-part buffers:
+//   copy thread (warp 18, lane 0), per sub-frame u:
+//     wait d1_full(u) -> copy tile part u+NB into the buffer S1(u) read (frames ahead -> L2)
+//   stage-1 issuer (warp 17, lane 0), per sub-frame u:
+//     wait b2_full(u) and tile part u+2 -> S1(u+2) -> d1_full[u&1]
+//   stage-2 issuer (warp 16, lane 0), per sub-frame u:
+//     wait b2_full(u) [and, at h = 0, d2_empty(t-1)] -> S2(u) -> b2_free[u&1] (H > 1),
+//     and at h = H-1 -> d2_full
+//   epilogue warps 0-15, per sub-frame u:
+//     wait d1_full(u) [and b2_free(u-2)] -> epilogue 1 (u) -> arrive b2_full[u&1];
+//     at h = 0: wait d2_full(t-1) -> epilogue 2 (t-1) -> arrive d2_empty
+// Epilogue 2 of frame t-1 runs after epilogue 1 of part 0 of frame t, before the later parts,
+// so the stage-2 chain of part 0 (which waits for it) never waits on a later epilogue 1.
 // Items are separated by two block-wide named barriers (operands loaded; item done).
 constexpr int kWs3Threads = 640;
 // Grid tiles requested into L2 this many frames before the shared-memory copy that
@@ -1908,6 +1956,7 @@ constexpr int kWs3Threads = 640;
 // stage-1 MMAs, which is less than the HBM latency; from L2 it arrives in time.
 constexpr int kTilePrefetch = 8;
 constexpr int kWs3MaxBlocks = 256;  // blocks per launch (one per SM) the split bookkeeping holds
+constexpr int kWs3MaxTileBufs = 4;  // tile-part buffers of k_dftgemm_ws3 (short row parts need more in flight)
 
 __device__ __forceinline__ void bar_all(int id)
 {
@@ -1973,7 +2022,8 @@ template <int MODE>  // 0: whole items, 1: equal shares (split items), 2: whole 
 __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bar_a, d1_full[2], b2_full[2], d2_full, d2_empty, tile_full[2];
+    __shared__ uint64_t bar_a, d1_full[2], b2_full[2], b2_free[2], d2_full, d2_empty, tile_full[kWs3MaxTileBufs],
+        drain[2];
     __shared__ uint32_t tmem_sh;
     __shared__ int err_sh;
     __shared__ int split_slot[kWs3MaxBlocks];  // partial slots of a split item, in block order
@@ -1988,8 +2038,10 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&d1_full[i], 1);
             tc::mbar_init(&b2_full[i], 16);
-            tc::mbar_init(&tile_full[i], 1);
+            tc::mbar_init(&b2_free[i], 1);
+            tc::mbar_init(&drain[i], 1);
         }
+        for (int i = 0; i < kWs3MaxTileBufs; ++i) tc::mbar_init(&tile_full[i], 1);
         tc::mbar_init(&d2_full, 1);
         tc::mbar_init(&d2_empty, 16);
         err_sh = 0;
@@ -2013,10 +2065,17 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 
     if (warp >= 16) {
         // ------------------------------------------------------------ control warpgroup
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
+        // 4 control warps x 32 lanes x 32 registers + 16 epilogue warps x 32 lanes x 112 =
+        // 61,440: exactly the 640 threads x 96 registers the block is launched with
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
         uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
-        const bool iss1 = warp == 17 && lane == 0;  // stage 1: A1, grid tiles, S1 chains
+        uint32_t pend = 0;  // copy thread: bulk copies in flight (bit j tile buffer j, bit 7 A1)
+        uint32_t cph = 0;   // copy thread: parity of the phase the next copy into buffer j (bit j)
+                            // or of A1 (bit 7) completes
+        const bool iss1 = warp == 17 && lane == 0;  // stage 1: S1 chains
         const bool iss2 = warp == 16 && lane == 0;  // stage 2 chains
+        const bool cpy = warp == 18 && lane == 0;   // A1 and tile-part copies, L2 prefetches
+        const int NB = a.nbt;                       // tile-part buffers in shared memory (2..4)
         long long w = wb0;
         for (int it = 0;; ++it) {
             int item, fs, nt;  // work item, its first frame and the frames of this segment
@@ -2035,76 +2094,105 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const int g = item % a.n_g, cl = item / (a.n_g * a.n_kb);
             const int c = a.c0 + cl;
             const int4 bx = a.box[c];
-            const int nxp = bx.z, nyp = bx.w;
-            const int K1 = 2 * nxp, K2 = 2 * nyp, N1 = P * nyp;
-            const uint32_t tile_bytes = (uint32_t)N1 * pad64(K1) * 2;
+            const int4 tp = a.tbox[c];
+            const int nxp = bx.z, nyh = tp.x, H = tp.y;
+            const int K1 = 2 * nxp, K2h = 2 * nyh, N1 = P * nyh;
+            const int NU = nt * H;  // sub-frames u = t H + h: frame t, row part h
+            const uint32_t part_bytes = (uint32_t)N1 * pad64(K1) * 2;
+            auto buf = [&](int b) { return sbase + a.sB1 + (size_t)b * a.b1_bytes; };
+            auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
+                const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
+                if (r) ph ^= 1u << slot;
+                return r;
+            };
+            // copy thread: A1 and the first NB tile parts now, then part u+NB once S1(u) has read
+            // its buffer (after the barrier: S1 is issued only past it)
             const size_t frame_step = (size_t)a.n_ch * a.tile_stride;
             const uint8_t* tiles_c = a.tiles + (size_t)cl * a.tile_stride + (size_t)fs * frame_step;
-            if (iss1) {
+            const uint8_t* nxt = tiles_c;  // next part to copy, advanced without division
+            int nxt_h = 0;
+            auto copy_next = [&](int b) {
+                tc::mbar_expect_tx(&tile_full[b], part_bytes);
+                tc::bulk_g2s(buf(b), nxt, part_bytes, &tile_full[b]);
+                pend |= 1u << b;
+                cph ^= 1u << b;
+                if (++nxt_h == H) {
+                    nxt_h = 0;
+                    nxt += frame_step - (size_t)(H - 1) * part_bytes;
+                } else {
+                    nxt += part_bytes;
+                }
+            };
+            if (cpy) {
                 const uint32_t a1_bytes = 256u * pad64(K1);
                 tc::mbar_expect_tx(&bar_a, a1_bytes);
                 tc::bulk_g2s(sA1, a.a1p + a.a1p_off[(size_t)c * a.n_g + g], a1_bytes, &bar_a);
-                for (int j = 0; j < 2 && j < nt; ++j) {
-                    tc::mbar_expect_tx(&tile_full[j], tile_bytes);
-                    tc::bulk_g2s(sbase + a.sB1 + (size_t)j * a.b1_bytes, tiles_c + (size_t)j * frame_step, tile_bytes,
-                                 &tile_full[j]);
-                }
-                for (int j = 2; j < 2 + kTilePrefetch && j < nt; ++j)  // later tiles: HBM -> L2 ahead of use
-                    tc::bulk_prefetch_l2(tiles_c + (size_t)j * frame_step, tile_bytes);
+                pend |= 0x80u;
+                cph ^= 0x80u;
+                for (int j = 0; j < NB && j < NU; ++j) copy_next(j);
+                for (int j = 1; j <= kTilePrefetch && j < nt; ++j)  // later frames: HBM -> L2 ahead of use
+                    tc::bulk_prefetch_l2(tiles_c + (size_t)j * frame_step, part_bytes * H);
             }
             bar_all(1);  // A2 is in TMEM
-            auto wait_bit = [&](uint64_t* bar, uint32_t& ph, int slot) -> bool {
-                const bool r = tc::mbar_wait(bar, (ph >> slot) & 1u, kWaitBudget);
-                ph ^= 1u << slot;
-                return r;
-            };
-            if (iss1) {  // per frame t: S1(t) done -> tile t+2 into its buffer; E1(t) done -> S1(t+2)
+            if (iss1) {  // per sub-frame u: E1(u) has read D1[u&1] and tile part u+2 is in -> S1(u+2)
                 const uint32_t id1 = tc::idesc_f16_f32(128, N1);
-                auto issue_s1 = [&](int t) {
-                    issue_ss(K1 / 16, tmem + (t & 1) * a.d1_cols, tc::smem_u32(sA1),
-                             tc::smem_u32(sbase + a.sB1 + (size_t)(t & 1) * a.b1_bytes), 128 * 128, N1 * 128, id1);
-                    tc::mma_commit(&d1_full[t & 1]);
+                auto issue_s1 = [&](int slot, int b) {
+                    issue_ss(K1 / 16, tmem + slot * a.d1_cols, tc::smem_u32(sA1), tc::smem_u32(buf(b)), 128 * 128,
+                             N1 * 128, id1);
+                    tc::mma_commit(&d1_full[slot]);
                 };
                 bool good = wait_bit(&bar_a, ph_a, 0);
-                for (int j = 0; j < 2 && j < nt && good; ++j) {
+                for (int j = 0; j < 2 && j < NU && good; ++j) {
                     good = wait_bit(&tile_full[j], ph_tile, j);
                     if (good) {
                         tc::fence_after_sync();
-                        issue_s1(j);
+                        issue_s1(j, j);
                     }
                 }
-                for (int t = 0; t < nt && good; ++t) {
-                    const int sl = t & 1;
-                    good = wait_bit(&d1_full[sl], ph_d1, sl);  // S1(t) done: its tile buffer is free
-                    if (good && t + 2 < nt) {
-                        tc::mbar_expect_tx(&tile_full[sl], tile_bytes);
-                        tc::bulk_g2s(sbase + a.sB1 + (size_t)sl * a.b1_bytes, tiles_c + (size_t)(t + 2) * frame_step,
-                                     tile_bytes, &tile_full[sl]);
+                int bu2 = 2 % NB;  // buffer of sub-frame u + 2
+                for (int u = 0; u < NU - 2 && good; ++u) {
+                    const int sl = u & 1;
+                    good = wait_bit(&b2_full[sl], ph_b2, sl);  // E1(u) has read D1[sl]
+                    if (good) good = wait_bit(&tile_full[bu2], ph_tile, bu2);
+                    if (good) {
+                        tc::fence_after_sync();
+                        issue_s1(sl, bu2);
                     }
-                    if (good && t + 2 + kTilePrefetch < nt)
-                        tc::bulk_prefetch_l2(tiles_c + (size_t)(t + 2 + kTilePrefetch) * frame_step, tile_bytes);
-                    if (good) good = wait_bit(&b2_full[sl], ph_b2, sl);  // E1(t) has read D1[sl]
-                    if (good && t + 2 < nt) {
-                        good = wait_bit(&tile_full[sl], ph_tile, sl);
-                        if (good) {
-                            tc::fence_after_sync();
-                            issue_s1(t + 2);
-                        }
-                    }
+                    if (++bu2 == NB) bu2 = 0;
                 }
+                for (int u = max(0, NU - 2); u < NU && good; ++u)  // the last two E1s, so parities stay paired
+                    good = wait_bit(&b2_full[u & 1], ph_b2, u & 1);
                 if (!good) err_sh = 1;
-            } else if (iss2) {  // per frame t: E1(t) wrote B2[t&1] and E2(t-1) read D2 -> S2(t)
+            } else if (iss2) {  // per sub-frame u: E1(u) wrote B2[u&1] (and E2(t-1) read D2) -> S2(u)
                 const uint32_t id2 = tc::idesc_f16_f32(128, 128 * P);
                 bool good = true;
-                for (int t = 0; t < nt && good; ++t) {
-                    const int sl = t & 1;
-                    good = wait_bit(&b2_full[sl], ph_b2, sl);
-                    if (good && t >= 1) good = wait_bit(&d2_empty, ph_e2, 0);
-                    if (!good) break;
-                    tc::fence_after_sync();
-                    issue_ts(K2 / 16, tmem + 256, tmem + a2col, tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes),
-                             R2 * 128, id2);
-                    tc::mma_commit(&d2_full);
+                for (int t = 0; t < nt && good; ++t)
+                    for (int h = 0; h < H && good; ++h) {
+                        const int sl = (t * H + h) & 1;
+                        good = wait_bit(&b2_full[sl], ph_b2, sl);
+                        if (good && h == 0 && t >= 1) good = wait_bit(&d2_empty, ph_e2, 0);
+                        if (!good) break;
+                        tc::fence_after_sync();
+                        issue_ts(K2h / 16, tmem + 256, tmem + a2col + h * nyh,
+                                 tc::smem_u32(sbase + a.sB2 + (size_t)sl * a.b2_bytes), R2 * 128, id2, h > 0);
+                        if (H > 1) tc::mma_commit(&b2_free[sl]);  // S2(u) has read B2[sl]
+                        if (h == H - 1) tc::mma_commit(&d2_full);
+                    }
+                if (!good) err_sh = 1;
+            } else if (cpy) {
+                bool good = true;
+                int bu = 0, hu = 0, tu = 0;  // buffer, row part and frame of u
+                for (int u = 0; u < NU && good; ++u) {
+                    good = wait_bit(&d1_full[u & 1], ph_d1, u & 1);  // S1(u) done: buffer bu is free
+                    if (good) pend &= ~((1u << bu) | 0x80u);  // its copy (and A1) had landed: S1(u) read them
+                    if (good && u + NB < NU) copy_next(bu);
+                    if (good && hu == 0 && tu + 1 + kTilePrefetch < nt)
+                        tc::bulk_prefetch_l2(tiles_c + (size_t)(tu + 1 + kTilePrefetch) * frame_step, part_bytes * H);
+                    if (++bu == NB) bu = 0;
+                    if (++hu == H) {
+                        hu = 0;
+                        ++tu;
+                    }
                 }
                 if (!good) err_sh = 1;
             }
@@ -2112,10 +2200,19 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             bar_all(2);  // item done
             if (err_sh) break;
         }
+        if (err_sh && (iss1 || iss2)) {  // a wait ran out: let this thread's MMAs finish (bounded)
+            tc::mma_commit(&drain[iss2 ? 1 : 0]);
+            tc::mbar_wait(&drain[iss2 ? 1 : 0], 0, kWaitBudget);
+        }
+        if (err_sh && cpy) {  // and the bulk copies in flight, before the block releases its memory
+            for (int j = 0; j < kWs3MaxTileBufs; ++j)  // a pending copy completes the phase before cph's
+                if ((pend >> j) & 1u) tc::mbar_wait(&tile_full[j], ((cph >> j) & 1u) ^ 1u, kWaitBudget);
+            if (pend & 0x80u) tc::mbar_wait(&bar_a, ((cph >> 7) & 1u) ^ 1u, kWaitBudget);
+        }
     } else {
         // ------------------------------------------------------------ epilogue warps
         asm volatile("setmaxnreg.inc.sync.aligned.u32 112;" ::: "memory");
-        uint32_t ph_d1 = 0, ph_d2 = 0;
+        uint32_t ph_d1 = 0, ph_d2 = 0, ph_bf = 0;
         const int q4 = warp & 3, j4 = warp >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
         const int h2 = j4 >> 1;
@@ -2137,13 +2234,11 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const bool first_seg = it == 0;
             const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
             const int c = a.c0 + cl;
-            const int4 bx = a.box[c];
-            const int nyp = bx.w;
-            const int K2 = 2 * nyp;
-            if (warp < 4) {  // stage-2 DFT operand -> TMEM (lane = ky row)
-                const uint32_t* src =
-                    a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * (K2 / 2);
-                for (int jj = 0; jj < K2 / 2; jj += 8) {
+            const int4 tp = a.tbox[c];
+            const int nyh = tp.x, H = tp.y, nyt = tp.z;
+            if (warp < 4) {  // stage-2 DFT operand (every row part) -> TMEM (lane = ky row)
+                const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * nyt;
+                for (int jj = 0; jj < nyt; jj += 8) {
                     uint32_t r[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
@@ -2159,7 +2254,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
             const int hh = q4 & 1;
             const bool imw = (q4 >> 1) != 0;
-            const int nyc = nyp >> 3;
+            const int nyc = nyh >> 3;
             int p1, yc0, yc1;
             if (P == 2) {
                 p1 = j4 >> 1;
@@ -2191,22 +2286,27 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) axx[i] = ayy[i] = arx[i] = aix[i] = 0.f;
             };
+            const int NU = nt * H;
             bool live = true;
-            for (int t = 0; t < nt && live; ++t) {
-                const int sl = t & 1;
-                const bool w = tc::mbar_wait(&d1_full[sl], (ph_d1 >> sl) & 1u, kWaitBudget);
+            for (int u = 0, t = 0, h = 0; u < NU && live; ++u) {
+                const int sl = u & 1;
+                bool w = tc::mbar_wait(&d1_full[sl], (ph_d1 >> sl) & 1u, kWaitBudget);
                 ph_d1 ^= 1u << sl;
+                if (w && H > 1 && u >= 2) {  // S2(u-2) has read B2[sl]
+                    w = tc::mbar_wait(&b2_free[sl], (ph_bf >> sl) & 1u, kWaitBudget);
+                    ph_bf ^= 1u << sl;
+                }
                 __syncwarp();
                 tc::fence_after_sync();
                 if (w)
-                    ws2_epilogue1<2>(tmem + lane_base + sl * a.d1_cols + p1 * nyp, nyp, yc0, yc1, imw, lane,
+                    ws2_epilogue1<2>(tmem + lane_base + sl * a.d1_cols + p1 * nyh, nyh, yc0, yc1, imw, lane,
                                   sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * P * hh + 64 * p1, R2);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&b2_full[sl]);
                 bool w2 = true;
-                if (t >= 1) {
+                if (h == 0 && t >= 1) {
                     w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
                     ph_d2 ^= 1u;
                     __syncwarp();
@@ -2219,10 +2319,19 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 }
                 if (!w || !w2) err_sh = 1;
                 live = !__any_sync(0xffffffffu, err_sh != 0);
+                if (++h == H) {
+                    h = 0;
+                    ++t;
+                }
             }
             if (nt > 0 && live) {
-                const bool w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
+                bool w2 = tc::mbar_wait(&d2_full, ph_d2 & 1u, kWaitBudget);
                 ph_d2 ^= 1u;
+                // the last two stage-2 steps' B2 releases, waited on by no later epilogue 1
+                for (int u = max(0, NU - 2); w2 && H > 1 && u < NU; ++u) {
+                    w2 = tc::mbar_wait(&b2_free[u & 1], (ph_bf >> (u & 1)) & 1u, kWaitBudget);
+                    ph_bf ^= 1u << (u & 1);
+                }
                 if (!w2) err_sh = 1;
                 __syncwarp();
                 tc::fence_after_sync();
@@ -2276,7 +2385,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 // chunk) take at most `budget` bytes, and the tile buffer for them.
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
 {
-    if (variant < 1 || variant > 3 || !p->tc.ws || (p->sub > 0 && variant != 3) ||
+    if (variant < 1 || variant > 3 || !p->tc.ws || ((p->sub > 0 || p->tc.parts) && variant != 3) ||
         (variant == 3 && p->sm_count > kWs3MaxBlocks))
         return EPIC_ERR_UNSUPPORTED;
     p->tc.ws_variant = variant;
@@ -2307,6 +2416,10 @@ epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
     p->scratch_bytes = 0;
     cudaError_t e = cudaMalloc(&p->scratch, bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(tensor path tile buffer)");
+    // zero once: tile bytes no gridding kernel writes (K padding past 2 nx) then hold zeros or
+    // FP16 values of other tiles, never stale non-finite bits, and meet zero DFT operands
+    e = cudaMemset(p->scratch, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemset(tensor path tile buffer)");
     p->scratch_bytes = bytes;
     return EPIC_OK;
 }
@@ -2417,22 +2530,49 @@ epic_status dftgemm_setup(epic_plan_s* p)
     };
     size_t sA1, sA2, sB1, sB2;
     const size_t limit = (size_t)p->smem_optin - 2048;
-    // warp-specialised variant (64-column pairs): A1 + 2 tiles + 2 double-width B2 buffers
-    {
-        const int tm = 2 * N1max + p->box_max_y;
-        const size_t b2w = align_up(2ull * 2 * 64 * P * K2max, 1024);
-        const size_t need_ws = align_up(256ull * K1max, 1024) + 2 * b1 + 2 * b2w;
-        p->tc.ws = tm <= 256 && need_ws <= limit;
-        if (p->tc.ws) {
-            p->tc.sA1 = 0;
-            p->tc.sB1 = (unsigned)align_up(256ull * K1max, 1024);
-            p->tc.sB2 = (unsigned)(p->tc.sB1 + 2 * b1);
-            p->tc.b1_bytes = (unsigned)b1;
-            p->tc.b2_bytes = (unsigned)b2w;
-            p->tc.d1_cols = N1max;
-            p->tc.smem = (int)(need_ws + 1024);
+    // warp-specialised variant (64-column pairs): A1 + NB tile parts + 2 B2 buffers in shared
+    // memory; 2 D1 slots + A2 + D2 in TMEM.  Each channel's box rows go in H_c parts of nyh_c
+    // rows (row_parts), chosen for the largest D1 slot width D that fits both memories.
+    p->tc.tbox_h.assign(C, make_int4(0, 0, 0, 0));
+    p->tc.parts = false;
+    p->tc.ws = false;
+    for (int D = 256; D >= 16 && !p->tc.ws; D -= 16) {
+        int dmax = 0, a2max = 0, nyh_max = 0;
+        bool ok = true, split = false;
+        std::vector<int4> tb(C);
+        for (int c = 0; c < C && ok; ++c) {
+            const int4 r = row_parts(p->box[c].ny, P, D);
+            if (r.y == 0) ok = false;
+            tb[c] = r;
+            dmax = std::max(dmax, P * r.x);
+            a2max = std::max(a2max, r.z);
+            nyh_max = std::max(nyh_max, r.x);
+            split = split || r.y > 1;
         }
+        if (!ok || 2 * dmax + a2max > 256) continue;
+        const size_t b1p = align_up(2ull * dmax * K1max, 1024);
+        const size_t b2w = align_up(2ull * 2 * 64 * P * pad64(2 * nyh_max), 1024);
+        // as many tile-part buffers (2..4) as fit: row parts are short steps, so more copies
+        // must be in flight to cover their latency
+        int nbt = 4;
+        auto need_for = [&](int nb) { return align_up(256ull * K1max, 1024) + nb * b1p + 2 * b2w; };
+        while (nbt > 2 && need_for(nbt) > limit) --nbt;
+        const size_t need_ws = need_for(nbt);
+        if (need_ws > limit) continue;
+        p->tc.ws = true;
+        p->tc.parts = split;
+        p->tc.tbox_h = tb;
+        p->tc.nbt = nbt;
+        p->tc.sA1 = 0;
+        p->tc.sB1 = (unsigned)align_up(256ull * K1max, 1024);
+        p->tc.sB2 = (unsigned)(p->tc.sB1 + nbt * b1p);
+        p->tc.b1_bytes = (unsigned)b1p;
+        p->tc.b2_bytes = (unsigned)b2w;
+        p->tc.d1_cols = dmax;
+        p->tc.smem = (int)(need_ws + 1024);
     }
+    if (!p->tc.ws)  // one part per channel for the other kernels' tile layout
+        for (int c = 0; c < C; ++c) p->tc.tbox_h[c] = make_int4(p->box[c].ny, 1, p->box[c].ny, 0);
     // fast variant: 2 D1 slots + A2 (FP16 pairs) in TMEM columns [0, 256); 3 tiles + 2 B2 in shared memory
     {
         const int tm = 2 * N1max + p->box_max_y;  // 2 N1 + K2/2 columns
@@ -2558,33 +2698,37 @@ epic_status dftgemm_setup(epic_plan_s* p)
         }
     }
     p->tc.n_gp = n_gp;
-    // row-major stage-2 operand as packed FP16 pairs (lower K in the low half) for TMEM
+    // row-major stage-2 operand as packed FP16 pairs (lower K in the low half) for TMEM, per
+    // row part: part h of a row holds words [h nyh, (h + 1) nyh), K = (re | im) of its nyh box
+    // rows; rows past the box (part padding) are zero
     std::vector<long long> a2w_off((size_t)C * n_kb);
     size_t nw = 0;
     for (int c = 0; c < C; ++c)
         for (int kb = 0; kb < n_kb; ++kb) {
             a2w_off[(size_t)c * n_kb + kb] = (long long)nw;
-            nw += 128ull * p->box[c].ny;  // K2/2 words per row
+            nw += 128ull * p->tc.tbox_h[c].z;  // H nyh words per row
         }
     std::vector<uint32_t> a2w(nw, 0);
     for (int c = 0; c < C; ++c) {
         const Box b = p->box[c];
+        const int nyh = p->tc.tbox_h[c].x, H = p->tc.tbox_h[c].y, nyt = p->tc.tbox_h[c].z;
         for (int kb = 0; kb < n_kb; ++kb) {
             uint32_t* t = &a2w[a2w_off[(size_t)c * n_kb + kb]];
             for (int r = 0; r < 128; ++r) {
                 const int ky = 128 * kb + r;
                 if (ky >= N) continue;
-                for (int j = 0; j < b.ny; ++j) {
-                    uint16_t h[2];
-                    for (int u = 0; u < 2; ++u) {
-                        const int k = 2 * j + u;
-                        const int y = b.y0 + (k % b.ny);
-                        double fr, fi;
-                        F(y, ky, &fr, &fi);
-                        h[u] = f16_bits(k < b.ny ? fr : fi);
+                for (int h = 0; h < H; ++h)
+                    for (int j = 0; j < nyh; ++j) {
+                        uint16_t hv[2];
+                        for (int u = 0; u < 2; ++u) {
+                            const int k = 2 * j + u;                           // K index within the part
+                            const int yb = h * nyh + (k < nyh ? k : k - nyh);  // box row
+                            double fr = 0.0, fi = 0.0;
+                            if (yb < b.ny) F(b.y0 + yb, ky, &fr, &fi);
+                            hv[u] = f16_bits(k < nyh ? fr : fi);
+                        }
+                        t[(size_t)r * nyt + h * nyh + j] = (uint32_t)hv[0] | ((uint32_t)hv[1] << 16);
                     }
-                    t[(size_t)r * b.ny + j] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-                }
             }
         }
     }
@@ -2608,6 +2752,9 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.a2_off, a2_off.size() * sizeof(long long));
     if (e == cudaSuccess)
         e = cudaMemcpy(p->tc.a2_off, a2_off.data(), a2_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc.tbox, (size_t)C * sizeof(int4));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->tc.tbox, p->tc.tbox_h.data(), (size_t)C * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->tc.status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(p, e, "tensor path table upload");
@@ -2622,7 +2769,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
 
     // chunking: channel groups big enough to fill the GPU, time chunks whose tiles fit the budget
     size_t stride = 0;
-    for (int c = 0; c < C; ++c) stride = std::max(stride, (size_t)P * p->box[c].ny * pad64(2 * p->box[c].nx) * 2);
+    for (int c = 0; c < C; ++c)
+        stride = std::max(stride, (size_t)P * p->tc.tbox_h[c].z * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
     const int per_ch = n_kb * (p->tc.ws ? n_gp : n_s);
     p->tc.cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
@@ -2708,7 +2856,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 const size_t nu = plist[u].size(), nv = plist[v].size();
                 return nu != nv ? nu > nv : morton(u) < morton(v);
             });
-            const int n1 = p->P * bx.ny;
+            const int nyh = p->tc.tbox_h[c].x;
+            const uint32_t part_bytes = (uint32_t)(p->P * nyh) * pad64(2 * bx.nx) * 2;
             std::vector<std::vector<int4>> gtasks;  // the 32 tasks of each group (padding tasks: no store)
             std::vector<int> gcost;
             for (size_t g0 = 0; g0 < idx.size(); g0 += 32) {
@@ -2729,8 +2878,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
                     const int q = idx[g0 + l];
                     if (q >= (1 << 24)) fits = false;
                     const int y = q / hp, x = kTaskCells * (q % hp);
-                    gt[l] = make_int4(q | (nmax << 24), base, (int)tile_half_off(y, x, n1),
-                                      (int)tile_half_off(y, bx.nx + x, n1));
+                    gt[l] = make_int4(q | (nmax << 24), base, (int)tile_part_off(y, x, nyh, p->P, part_bytes),
+                                      (int)tile_part_off(y, bx.nx + x, nyh, p->P, part_bytes));
                 }
                 gtasks.push_back(gt);
                 gcost.push_back(nmax + 1);  // list steps + the tile stores
@@ -2847,6 +2996,10 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2>, p->smem_optin);
     p->tc.ws_variant = p->tc.ws ? 3 : 0;
     if (p->tc.ws && p->sm_count > kWs3MaxBlocks) p->tc.ws_variant = 1;
+    if (p->tc.parts && p->tc.ws_variant != 3) {
+        p->last_error = "tensor path: an occupied grid this tall needs the control-warp kernel";
+        return EPIC_ERR_UNSUPPORTED;
+    }
     if (p->sub > 0 && p->tc.ws_variant != 3) {
         p->last_error = "tensor path: sub-integrations need a control-warp kernel (occupied grid too large)";
         return EPIC_ERR_UNSUPPORTED;
@@ -2896,6 +3049,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     a.d1_cols = p->tc.d1_cols;
     a.a1p = p->tc.a1p;
     a.a1p_off = p->tc.a1p_off;
+    a.tbox = p->tc.tbox;
+    a.nbt = p->tc.nbt;
     const int fpc = kGridFramesPerBlock;
     const int F = p->tc.grid_frames;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
@@ -2925,6 +3080,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 g.max_list = p->tc.grid_max_list;
                 g.bits = p->bits;
                 g.jones = p->dt.jones;
+                g.tbox = p->tc.tbox;
                 g.bulk = ((A * P * (p->bits / 4)) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
                 const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
                 ev_begin(p, "k_dftgemm_grid", s);
@@ -2971,7 +3127,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     k_dftgemm_grid<CS, FF><<<gg, kThreads, p->tc.grid_smem, s>>>(volt, t0, c0, ng, nt, fpc, C, A, P, p->bits,         \
                                                               p->dt.box,                                               \
                                                               p->dt.cell_off, p->dt.cell_ptr, p->dt.contrib_e,         \
-                                                              p->dt.contrib_w, p->dt.jones, (uint8_t*)p->scratch,     \
+                                                              p->dt.contrib_w, p->dt.jones, p->tc.tbox,                \
+                                                              (uint8_t*)p->scratch,                                    \
                                                               p->tc.stride)
             if (p->tc.grid_csr_smem) {
                 if (F == 4) EPIC_GRID_LAUNCH(true, 4);

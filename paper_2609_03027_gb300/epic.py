@@ -73,7 +73,7 @@ class _PlanInfo(ctypes.Structure):
                 ("box_max_y", ctypes.c_int), ("time_chunk", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
                 ("scratch_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int),
                 ("gemm_flops_per_sample", ctypes.c_double), ("input_bits", ctypes.c_int), ("sub_int", ctypes.c_int),
-                ("pol_mix", ctypes.c_int)]
+                ("pol_mix", ctypes.c_int), ("tc_kernel", ctypes.c_int), ("row_parts", ctypes.c_int)]
 
 
 _lock = threading.Lock()

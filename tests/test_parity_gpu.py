@@ -259,3 +259,48 @@ def test_polarisation_mixing_kernels(path, bits, sub):
     assert np.abs(sw[..., 3, :, :] + base[..., 3, :, :]).max() <= 1e-6 * np.abs(base[..., :2, :, :]).max()
     with E.Plan.from_config(mixed, path=path) as plan:
         assert plan.info()["pol_mix"] == 1
+
+
+TALL = {
+    # name: (A, C, P, N, K, T, diameter_m, extra); occupied boxes 54-93 rows tall, so the
+    # tensor path cuts them into row parts (channels of one plan into different numbers)
+    "dual-pol": (80, 3, 2, 128, 5, 7, 85.0, {}),
+    "dual-pol-wide-gcf": (64, 2, 2, 128, 7, 4, 80.0, {"freq_scaled": True}),
+    "single-pol": (60, 2, 1, 128, 3, 5, 100.0, {}),
+    "n256": (200, 2, 2, 256, 3, 3, 88.0, {}),
+    "dual-pol-sub-int": (70, 2, 2, 128, 5, 9, 85.0, {"sub_int": 3}),
+    "dual-pol-8bit-mixed": (50, 2, 2, 128, 3, 4, 90.0, {"bits": 8, "jones": True}),
+}
+
+
+@pytest.mark.parametrize("split", [-1, 0, 1])
+@pytest.mark.parametrize("case", list(TALL))
+def test_tall_boxes_in_row_parts(case, split):
+    # occupied grids too tall for the stage-1 results, the stage-2 operand and the stage-2
+    # result to sit in tensor memory at once go through the warp-specialised kernel in parts
+    # of rows; stage 2 adds the parts up (Eq. 1's sum over the grid rows)
+    A, C, P, N, K, T, diam, extra = TALL[case]
+    cfg = synth.small_config(n_ant=A, n_chan=C, n_pol=P, grid_n=N, gcf_k=K, n_time=T, seed=300 + A,
+                             diameter_m=diam, freq_scaled=extra.get("freq_scaled", False), sigma=0.7)
+    cfg = dataclasses.replace(cfg, input_bits=extra.get("bits", 4), sub_int=extra.get("sub_int", 0))
+    if extra.get("jones"):
+        cfg = dataclasses.replace(cfg, jones=synth.make_jones(cfg, seed=9, gain_rms=0.2, leak_rms=0.2))
+    if split == 1 and cfg.sub_int:
+        pytest.skip("sub-integrations run whole items")
+    v = synth.random_bytes((T, C, A, P) + ((2,) if cfg.input_bits == 8 else ()), seed=A + T)
+    ref = oracle_image(cfg, v)
+    with E.Plan.from_config(cfg, path="dftgemm", max_time=T) as plan:
+        info = plan.info()
+        assert info["tc_kernel"] == 3 and info["row_parts"] >= 2, info
+        if not cfg.sub_int:
+            plan.set_param("split", split)
+        d = torch.from_numpy(v).cuda()
+        got = plan.image(d).cpu().numpy()
+        plan.sync()
+        again = plan.image(d).cpu().numpy()
+    assert np.array_equal(got, again)
+    if cfg.sub_int:
+        for k in range(ref.shape[0]):
+            assert_parity(got[k], ref[k], "dftgemm", f"{case} set {k}")
+    else:
+        assert_parity(got, ref, "dftgemm", case)
