@@ -271,21 +271,14 @@ def run_e2e(E, cfg, volt, out, T, units, world, dev, args, tuning=None):
 
 # ----------------------------------------------------------------------------- serving (streaming mix)
 
-SERVE_CHANNELS = (32, 64, 128, 256, 384)
-SERVE_DF_HZ = 25e3
+SERVE_CHANNELS = synth.SERVE_CHANNELS
 
 
 def serving_plans_spec():
-    """(name, config) of every (station type, channel count) of the streaming mix: the
+    """Config of every (station type, channel count) of the streaming mix: the
     64/256/1024/4096-element station types, C contiguous 25 kHz channels from each
     type's first frequency."""
-    out = []
-    for st in synth.mixed_station_types():
-        for C in SERVE_CHANNELS:
-            cfg = dataclasses.replace(st, name=f"{st.name}-{C}ch")
-            cfg.freq_hz = st.freq_hz[0] + np.arange(C) * SERVE_DF_HZ
-            out.append(cfg)
-    return out
+    return [synth.serving_config(st, C) for st in synth.mixed_station_types() for C in SERVE_CHANNELS]
 
 
 def run_serving(E, args, dev):

@@ -284,3 +284,16 @@ def mixed_station_types() -> List[EpicConfig]:
     c4 = config(4)
     s4096 = dataclasses.replace(c4, name="mix-4096el-256grid", seed=54)
     return [s64, s256, s1024, s4096]
+
+
+SERVE_CHANNELS = (32, 64, 128, 256, 384)
+SERVE_DF_HZ = 25e3
+
+
+def serving_config(station: EpicConfig, n_chan: int) -> EpicConfig:
+    """A block of the streaming mix: `station` (one of mixed_station_types()) with n_chan
+    contiguous 25 kHz channels from the station's first frequency (the mix's channel
+    plan; the text gives none)."""
+    cfg = dataclasses.replace(station, name=f"{station.name}-{n_chan}ch")
+    cfg.freq_hz = station.freq_hz[0] + np.arange(n_chan) * SERVE_DF_HZ
+    return cfg

@@ -94,7 +94,7 @@ typedef struct {
     int n_ant;              /* elements A >= 1                                                    */
     const double* pos_m;    /* host [n_ant][2] x, y in metres                                     */
     int n_pol;              /* 1 or 2                                                             */
-    int n_chan;             /* channels C >= 1                                                    */
+    int n_chan;             /* channels C >= 1, C x n_pol <= 65535                                */
     const double* freq_hz;  /* host [n_chan] centre frequency of each channel, > 0                */
     const double* cell_m;   /* host [n_chan] grid spacing Delta_c, or NULL for lambda_c / 2       */
     int grid_n;             /* N: power of two, 8..512                                            */
@@ -179,12 +179,25 @@ epic_status epic_image(epic_plan_t plan, const uint8_t* volt, int T, void* strea
 /* Same as epic_image with HOST buffers: copies volt_host (T*C*A*P bytes) to the
  * plan's device staging buffer, images it, copies the images to out_host
  * (C*n_prod*N*N floats; with EPIC_ACCUMULATE its old content is uploaded first)
- * and synchronises the stream before returning.  Pinned host memory is fastest. */
+ * and synchronises the stream before returning.  Pinned host memory is fastest.
+ * Returns EPIC_ERR_TIMEOUT when a bounded device-side wait ran out during this call
+ * (or during an earlier call of the plan not yet reported by epic_sync). */
 epic_status epic_image_host(epic_plan_t plan, const uint8_t* volt_host, int T, void* stream,
                             float* out_host, unsigned flags);
 
-/* Wait for the plan's last stream and report any asynchronous CUDA error. */
+/* Wait for the plan's last stream and report any asynchronous CUDA error, or
+ * EPIC_ERR_TIMEOUT when a bounded device-side wait of one of the plan's kernels
+ * ran out since the last report (the images of that call are incomplete; the
+ * plan stays usable).  The flag is read and cleared here and by epic_image_host. */
 epic_status epic_sync(epic_plan_t plan);
+
+/* Failure-detection self-test: on `stream`, one block that holds tensor memory
+ * waits budget_cycles (1..4e9 SM clock cycles) on a barrier nothing signals, then
+ * raises the plan's bounded-wait flag, frees its tensor memory and returns -- the
+ * path the tensor-core kernels take when a wait runs out.  A following epic_sync
+ * (or epic_image_host) returns EPIC_ERR_TIMEOUT.  Nothing traps or faults.  The
+ * paper has no counterpart: it checks this implementation's own error handling. */
+epic_status epic_selftest_bounded_wait(epic_plan_t plan, long long budget_cycles, void* stream);
 
 /* Kernel durations (ms) of the last call made with EPIC_TIME_KERNELS, in launch
  * order, with static kernel names.  Synchronises on the recorded events.
@@ -267,11 +280,16 @@ epic_status epic_image_static_scratch(epic_plan_t plan, const uint8_t* volt, int
  * (one plan per station type) are admitted as they arrive and imaged
  * concurrently: each block waits until one of max_slots CUDA streams is free,
  * a range of the server's device pool (max_device_bytes, allocated once at
- * creation) holds it, and its plan is idle -- blocks of one plan run one at a
- * time in submission order, blocks of different plans overlap on the device.
+ * creation) holds it, and no earlier block with the same output images is still
+ * queued or running -- blocks that write one set of images run in submission
+ * order, all others (those of one plan included) overlap on the device.  Each
+ * slot has its own call memory (a plan's grid / tile scratch and bookkeeping),
+ * allocated the first time the slot runs a plan that needs more: up to max_slots
+ * times the largest plan scratch (epic_plan_info.scratch_bytes) besides the pool.
  * Images go to caller-owned device accumulators (use EPIC_ACCUMULATE to continue
  * an integration across blocks).  Latency of a block = wall time from submission
- * to completion of its kernels.  A plan given to a server must not be used by
+ * to completion of its kernels.  A block whose bounded device wait ran out
+ * completes with EPIC_ERR_TIMEOUT.  A plan given to a server must not be used by
  * other epic_image calls until its blocks are done.  The server's streams do not
  * wait for work the caller queued on other streams: the accumulators must be
  * complete (e.g. the caller's stream synchronised) when a block is submitted.
@@ -294,8 +312,10 @@ epic_status epic_server_submit(epic_server_t server, epic_plan_t plan, const uin
  * block's status and its latency in ms). */
 epic_status epic_server_poll(epic_server_t server, uint64_t ticket, int* done, double* latency_ms);
 
-/* Block up to timeout_ms for a ticket, then release it (EPIC_ERR_TIMEOUT if not done;
- * EPIC_ERR_NOT_FOUND for an unknown or already released ticket). */
+/* Block up to timeout_ms for a ticket, then release it and return the block's
+ * status (EPIC_ERR_TIMEOUT if not done in time; EPIC_ERR_NOT_FOUND for an unknown or
+ * already released ticket -- when several threads wait on one ticket, one of them
+ * collects it and the others get EPIC_ERR_NOT_FOUND). */
 epic_status epic_server_wait(epic_server_t server, uint64_t ticket, int timeout_ms, double* latency_ms);
 
 /* Completed blocks so far, p50 / p99 of their latencies (ms; -1 when none), blocks

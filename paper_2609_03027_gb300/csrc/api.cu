@@ -195,6 +195,7 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     if (d->n_ant < 1 || !d->pos_m) return bad("n_ant must be >= 1 and pos_m non-NULL");
     if (d->n_pol != 1 && d->n_pol != 2) return bad("n_pol must be 1 or 2");
     if (d->n_chan < 1 || !d->freq_hz) return bad("n_chan must be >= 1 and freq_hz non-NULL");
+    if ((long long)d->n_chan * d->n_pol > 65535) return bad("n_chan x n_pol must be at most 65535");
     if (!is_pow2(d->grid_n) || d->grid_n < 8 || d->grid_n > 512) return bad("grid_n must be a power of two in 8..512");
     if (d->max_time < 1) return bad("max_time must be >= 1");
     if (d->gcf.K < 1 || d->gcf.K > 8 || d->gcf.K > d->grid_n) return bad("gcf.K must be in 1..8");
@@ -323,7 +324,11 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
         free_plan(p);
         return st;
     }
-    e = cudaDeviceSynchronize();
+    if (!p->tc.status) {  // every plan has a bounded-wait flag (the tensor path's kernels set it)
+        e = cudaMalloc(&p->tc.status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->tc.status, 0, sizeof(int));
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         st = epic::cuda_fail(p, e, "plan setup");
         free_plan(p);
@@ -391,9 +396,74 @@ epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     }
     return EPIC_ERR_INVALID_ARG;
 }
+
+void call_scratch_free(CallScratch& c)
+{
+    cudaFree(c.scratch);
+    cudaFree(c.partial);
+    cudaFree(c.counters);
+    cudaFree(c.status);
+    c = CallScratch{};
+}
+
+epic_status call_scratch_fit(epic_plan_s* p, CallScratch& c)
+{
+    const size_t partial = p->tc.partial ? (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float) : 0;
+    auto grow = [&](void** ptr, size_t* have, size_t need, const char* what) -> epic_status {
+        if (need <= *have && (*ptr || need == 0)) return EPIC_OK;
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+        cudaError_t e = cudaMalloc(ptr, need);
+        if (e == cudaSuccess) e = cudaMemset(*ptr, 0, need);
+        if (e != cudaSuccess) return cuda_fail(p, e, what);
+        *have = need;
+        return EPIC_OK;
+    };
+    size_t counters_bytes = c.n_counters * sizeof(int), status_bytes = c.status ? sizeof(int) : 0;
+    epic_status st = grow(&c.scratch, &c.scratch_bytes, p->scratch_bytes, "cudaMalloc(call scratch)");
+    if (st == EPIC_OK) st = grow((void**)&c.partial, &c.partial_bytes, partial, "cudaMalloc(call partial sums)");
+    if (st == EPIC_OK)
+        st = grow((void**)&c.counters, &counters_bytes, p->tc.n_counters * sizeof(int), "cudaMalloc(call counters)");
+    c.n_counters = counters_bytes / sizeof(int);
+    if (st == EPIC_OK) st = grow((void**)&c.status, &status_bytes, sizeof(int), "cudaMalloc(call status)");
+    return st;
+}
+
+epic_status image_run_with(epic_plan_s* p, CallScratch& c, const uint8_t* volt, int T, cudaStream_t s, float* out,
+                           unsigned flags)
+{
+    // the kernels take these pointers as launch arguments, so swapping them around the
+    // launches is all it takes (calls of one plan come from one host thread)
+    std::swap(p->scratch, c.scratch);
+    std::swap(p->tc.partial, c.partial);
+    std::swap(p->tc.counters, c.counters);
+    std::swap(p->tc.status, c.status);
+    const epic_status st = image_run(p, volt, T, s, out, flags);
+    std::swap(p->scratch, c.scratch);
+    std::swap(p->tc.partial, c.partial);
+    std::swap(p->tc.counters, c.counters);
+    std::swap(p->tc.status, c.status);
+    return st;
+}
 }  // namespace epic
 
 extern "C" {
+
+// Read and clear the plan's bounded-wait flag once the calls that may set it are complete:
+// EPIC_ERR_TIMEOUT when a kernel's wait ran out since the flag was last cleared.
+static epic_status take_timeout(epic_plan_t p)
+{
+    if (!p->tc.status) return EPIC_OK;
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, p->tc.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "bounded-wait flag");
+    if (!flag) return EPIC_OK;
+    e = cudaMemset(p->tc.status, 0, sizeof(int));
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "bounded-wait flag");
+    p->last_error = "a device-side bounded wait ran out; the images of that call are incomplete";
+    return EPIC_ERR_TIMEOUT;
+}
 
 // Timing events the recorded graph will need (created before recording).
 static void reserve_events(epic_plan_t p, int T)
@@ -544,7 +614,7 @@ epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void
     if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemcpyAsync(D2H)");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaStreamSynchronize");
-    return EPIC_OK;
+    return take_timeout(p);  // the call is complete: report (and clear) a bounded wait that ran out
 }
 
 epic_status epic_sync(epic_plan_t p)
@@ -553,17 +623,7 @@ epic_status epic_sync(epic_plan_t p)
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return epic::cuda_fail(p, e, "epic_sync");
-    if (p->tc.status) {
-        int flag = 0;
-        e = cudaMemcpy(&flag, p->tc.status, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return epic::cuda_fail(p, e, "epic_sync(status)");
-        if (flag) {
-            cudaMemset(p->tc.status, 0, sizeof(int));
-            p->last_error = "a device-side bounded wait ran out; the images of that call are incomplete";
-            return EPIC_ERR_TIMEOUT;
-        }
-    }
-    return EPIC_OK;
+    return take_timeout(p);
 }
 
 epic_status epic_kernel_times(epic_plan_t p, const char** names, float* ms, int max, int* n_out)

@@ -82,6 +82,21 @@ struct TcState {
     int4* tbox = nullptr;          // same, on the device (every tensor-path plan)
     bool parts = false;            // some channel has H > 1 (only k_dftgemm_ws3 takes it)
     int nbt = 2;                   // k_dftgemm_ws3: tile-part buffers in shared memory (2..4)
+    size_t n_counters = 0;         // entries of `counters`
+};
+
+// Device memory one epic_image call writes besides its images: the grid / tile scratch, the
+// tensor path's split bookkeeping (partial sums, per-item counters, which the last block of
+// an item resets to zero) and the bounded-wait flag.  A plan owns one set; the streaming
+// server gives each of its slots its own, so that calls of one plan overlap on the device.
+struct CallScratch {
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    float* partial = nullptr;
+    size_t partial_bytes = 0;
+    int* counters = nullptr;
+    size_t n_counters = 0;
+    int* status = nullptr;
 };
 
 struct KernelEvent {
@@ -166,6 +181,12 @@ void ev_end(epic_plan_s* p, cudaStream_t s);
 epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);
 // one epic_image call after argument checks (flags without EPIC_GRAPH handling)
 epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags);
+// Grow c (zeroed on allocation) to what a call of p needs; allocates, so not on a hot path.
+epic_status call_scratch_fit(epic_plan_s* p, CallScratch& c);
+void call_scratch_free(CallScratch& c);
+// image_run with c's memory in place of the plan's (same host thread as every other call of p)
+epic_status image_run_with(epic_plan_s* p, CallScratch& c, const uint8_t* volt, int T, cudaStream_t s, float* out,
+                           unsigned flags);
 
 // k_plain.cu
 epic_status plain_setup(epic_plan_s* p);

@@ -3009,6 +3009,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
         e = cudaMalloc(&p->tc.partial, (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&p->tc.counters, n_items * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->tc.counters, 0, n_items * sizeof(int));
+        if (e == cudaSuccess) p->tc.n_counters = n_items;
         if (e == cudaSuccess)
             p->dt.dft_bytes += (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float) + n_items * sizeof(int);
     }

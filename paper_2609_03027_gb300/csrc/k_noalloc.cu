@@ -222,7 +222,13 @@ extern "C" epic_status epic_image_static_scratch(epic_plan_t p, const uint8_t* v
         return EPIC_OK;
     }
     float2* grid = static_cast<float2*>(scratch);
-    const int chunk = (int)std::max<size_t>(1, kStaticScratchBytes / per_t);
+    // time samples per chunk: what fits the array, and at most 65,535 (sample, channel, pol)
+    // columns of the column-FFT launch's second grid dimension
+    if ((size_t)C * P > 65535) {
+        p->last_error = "static-scratch imaging: more than 65,535 channel-polarisations";
+        return EPIC_ERR_UNSUPPORTED;
+    }
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(kStaticScratchBytes / per_t, 65535 / ((size_t)C * P)));
     for (int t0 = 0; t0 < T; t0 += chunk) {
         const int nt = std::min(chunk, T - t0);
         k_na_grid<<<dim3(nt, C), kNaThreads, sg, s>>>(volt, t0, C, A, P, N, p->dt.box, p->dt.cell_off, p->dt.cell_ptr,

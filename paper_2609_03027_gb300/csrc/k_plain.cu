@@ -193,8 +193,14 @@ size_t cols_smem(int N) { return sizeof(float2) * ((size_t)N / 2 + 2ull * col_ti
 epic_status plain_set_chunk(epic_plan_s* p, size_t budget)
 {
     const size_t per_t = (size_t)p->C * p->P * p->N * p->N * sizeof(float2);
-    int tcn = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->max_time, budget / per_t));
+    // at most 65,535 (sample, channel, pol) columns: the second grid dimension of the column FFT
+    const size_t max_t = 65535 / ((size_t)p->C * p->P);
+    int tcn = (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>((size_t)p->max_time, max_t), budget / per_t));
     if (p->sub > 0) tcn = std::max(p->sub, tcn - tcn % p->sub);  // whole sub-integrations per chunk
+    if ((size_t)tcn > max_t) {
+        p->last_error = "plain path: sub_int x n_chan x n_pol exceeds 65,535";
+        return EPIC_ERR_UNSUPPORTED;
+    }
     const size_t bytes = per_t * tcn;
     p->chunk_budget = budget;
     if (p->scratch && bytes == p->scratch_bytes) {

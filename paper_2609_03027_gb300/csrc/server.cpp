@@ -1,14 +1,18 @@
 // Streaming server: continuous batching of voltage blocks from several stations
 // (each with its own plan) onto one GPU.  The server owns one device pool,
-// carved first-fit into per-block ranges, and a set of slots (CUDA streams).  A
-// submitted block waits in a queue until a slot is free, pool memory for it is
-// free and its plan is idle (a plan's scratch belongs to one call at a time, so
-// blocks of one plan run in submission order); then its host block is copied
-// into its range and imaged on the slot's stream.  Blocks of different plans
-// therefore overlap on the device.  Images stay on the device in caller-owned
-// accumulators (EPIC_ACCUMULATE continues an integration).  The latency of a
-// block is the wall time from submission to the completion of its kernels,
-// taken in a stream host callback.
+// carved first-fit into per-block ranges, and a set of slots (CUDA streams),
+// each with its own call memory (grid / tile scratch, split bookkeeping and a
+// bounded-wait flag, sized for the largest plan it has run).  A submitted block
+// waits in a queue until a slot is free, pool memory for it is free and no
+// earlier block with the same output images is queued or running (blocks that
+// accumulate into one set of images run in submission order); then its host
+// block is copied into its range and imaged on the slot's stream with the slot's
+// call memory.  Blocks therefore overlap on the device, those of one plan
+// included.  Images stay on the device in caller-owned accumulators
+// (EPIC_ACCUMULATE continues an integration).  The latency of a block is the
+// wall time from submission to the completion of its kernels, taken in a
+// stream host callback, which also reads the slot's bounded-wait flag (copied
+// to pinned host memory behind the block's kernels) into the block's status.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +34,8 @@ constexpr size_t kAlign = 256;
 
 struct Job {
     uint64_t ticket = 0;
+    int waiters = 0;                // threads inside epic_server_wait for this ticket
+    bool released = false;          // collected by a waiter: no longer in the ticket map
     epic_plan_t plan = nullptr;
     int T = 0;
     float* out = nullptr;
@@ -59,12 +65,14 @@ struct epic_server_s {
     std::vector<cudaStream_t> streams;
     std::vector<Job*> slot_job;
     std::vector<Callback> callbacks;
+    std::vector<epic::CallScratch> slot_mem;  // call memory of each slot
+    int* slot_flag = nullptr;                 // pinned host copies of the slots' bounded-wait flags
     std::mutex mu;
     std::condition_variable cv;       // dispatcher wake-up
     std::condition_variable done_cv;  // ticket waiters
     std::deque<Job*> pending;
     std::map<uint64_t, Job*> jobs;
-    std::vector<epic_plan_t> busy_plans;
+    std::vector<float*> busy_outs;    // output images of the blocks on the device
     std::vector<double> latencies;
     size_t queue_limit = 0;
     uint64_t next_ticket = 1;
@@ -102,9 +110,9 @@ void pool_free(epic_server_s* s, size_t off)
         }
 }
 
-bool plan_busy(epic_server_s* s, epic_plan_t p)
+bool out_busy(epic_server_s* s, float* out)
 {
-    return std::find(s->busy_plans.begin(), s->busy_plans.end(), p) != s->busy_plans.end();
+    return std::find(s->busy_outs.begin(), s->busy_outs.end(), out) != s->busy_outs.end();
 }
 
 // Host callback after a block's kernels: bookkeeping only (no CUDA calls allowed here).
@@ -117,10 +125,11 @@ void CUDART_CB on_complete(void* arg)
         Job* j = s->slot_job[cb->slot];
         if (j) {
             j->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - j->submitted).count();
+            if (s->slot_flag[cb->slot]) j->status = EPIC_ERR_TIMEOUT;  // a bounded device wait ran out
             j->done = true;
             s->latencies.push_back(j->latency_ms);
             pool_free(s, j->off);
-            s->busy_plans.erase(std::find(s->busy_plans.begin(), s->busy_plans.end(), j->plan));
+            s->busy_outs.erase(std::find(s->busy_outs.begin(), s->busy_outs.end(), j->out));
             s->slot_job[cb->slot] = nullptr;
         }
     }
@@ -128,15 +137,15 @@ void CUDART_CB on_complete(void* arg)
     s->done_cv.notify_all();
 }
 
-// Pick the first startable job (FIFO per plan), reserve its slot, range and plan.
+// Pick the first startable job (FIFO per output), reserve its slot, range and output.
 Job* select_locked(epic_server_s* s)
 {
-    std::vector<epic_plan_t> seen;
+    std::vector<float*> seen;
     for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
         Job* j = *it;
-        const bool first_of_plan = std::find(seen.begin(), seen.end(), j->plan) == seen.end();
-        seen.push_back(j->plan);
-        if (!first_of_plan || plan_busy(s, j->plan)) continue;
+        const bool first_of_out = std::find(seen.begin(), seen.end(), j->out) == seen.end();
+        seen.push_back(j->out);
+        if (!first_of_out || out_busy(s, j->out)) continue;
         int slot = -1;
         for (size_t k = 0; k < s->slot_job.size(); ++k)
             if (!s->slot_job[k]) {
@@ -149,7 +158,7 @@ Job* select_locked(epic_server_s* s)
         j->off = off;
         j->slot = slot;
         s->slot_job[slot] = j;
-        s->busy_plans.push_back(j->plan);
+        s->busy_outs.push_back(j->out);
         s->pending.erase(it);
         return j;
     }
@@ -170,11 +179,21 @@ void worker_loop(epic_server_s* s)
         const int slot = j->slot;
         cudaStream_t st = s->streams[slot];
         uint8_t* dev = s->pool + j->off;
-        epic_status status = EPIC_OK;
+        epic::CallScratch& mem = s->slot_mem[slot];
+        // the slot's call memory grows to the plan's needs (the slot's previous block is done)
+        epic_status status = epic::call_scratch_fit(j->plan, mem);
         cudaError_t e = cudaSuccess;
-        if (j->bytes) e = cudaMemcpyAsync(dev, j->host, j->bytes, cudaMemcpyHostToDevice, st);
+        if (status == EPIC_OK) e = cudaMemsetAsync(mem.status, 0, sizeof(int), st);
+        if (e == cudaSuccess && j->bytes) e = cudaMemcpyAsync(dev, j->host, j->bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) status = EPIC_ERR_CUDA;
-        if (status == EPIC_OK) status = epic_image(j->plan, dev, j->T, st, j->out, j->flags);
+        if (status == EPIC_OK) {
+            if (j->T > 0) status = epic::image_run_with(j->plan, mem, dev, j->T, st, j->out, j->flags);
+            else status = epic_image(j->plan, dev, 0, st, j->out, j->flags);
+        }
+        if (status == EPIC_OK) {
+            e = cudaMemcpyAsync(&s->slot_flag[slot], mem.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) status = EPIC_ERR_CUDA;
+        }
         if (status == EPIC_OK) {
             e = cudaLaunchHostFunc(st, on_complete, &s->callbacks[slot]);
             if (e != cudaSuccess) {
@@ -189,7 +208,7 @@ void worker_loop(epic_server_s* s)
             j->done = true;
             j->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - j->submitted).count();
             pool_free(s, j->off);
-            s->busy_plans.erase(std::find(s->busy_plans.begin(), s->busy_plans.end(), j->plan));
+            s->busy_outs.erase(std::find(s->busy_outs.begin(), s->busy_outs.end(), j->out));
             s->slot_job[slot] = nullptr;
             s->done_cv.notify_all();
         }
@@ -220,12 +239,21 @@ epic_status epic_server_create(size_t max_device_bytes, int max_slots, epic_serv
     s->streams.assign(max_slots, nullptr);
     s->slot_job.assign(max_slots, nullptr);
     s->callbacks.resize(max_slots);
+    s->slot_mem.resize(max_slots);
+    if (cudaMallocHost(&s->slot_flag, sizeof(int) * max_slots) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->pool);
+        delete s;
+        return EPIC_ERR_OOM;
+    }
+    for (int k = 0; k < max_slots; ++k) s->slot_flag[k] = 0;
     for (int k = 0; k < max_slots; ++k) {
         s->callbacks[k] = Callback{s, k};
         if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
             for (auto st : s->streams)
                 if (st) cudaStreamDestroy(st);
             cudaFree(s->pool);
+            cudaFreeHost(s->slot_flag);
             delete s;
             return EPIC_ERR_CUDA;
         }
@@ -242,6 +270,13 @@ epic_status epic_server_submit(epic_server_t s, epic_plan_t plan, const uint8_t*
     if (!s || !plan || !out_dev || !ticket || T < 0 || T > plan->max_time || (T > 0 && !volt_host) ||
         (flags & ~(EPIC_ACCUMULATE | EPIC_TIME_KERNELS)))
         return EPIC_ERR_INVALID_ARG;
+    if (plan->sub > 0 && T % plan->sub != 0) return EPIC_ERR_INVALID_ARG;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, out_dev) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return EPIC_ERR_INVALID_ARG;  // the images must be device memory
+    }
     const size_t bytes = (size_t)T * plan->C * plan->A * plan->P * (plan->bits / 4);
     if (round_up(bytes) > s->pool_bytes) return EPIC_ERR_OOM;
     Job* j = new (std::nothrow) Job();
@@ -286,12 +321,20 @@ epic_status epic_server_wait(epic_server_t s, uint64_t ticket, int timeout_ms, d
     auto it = s->jobs.find(ticket);
     if (it == s->jobs.end()) return EPIC_ERR_NOT_FOUND;
     Job* j = it->second;
-    if (!s->done_cv.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] { return j->done; }))
-        return EPIC_ERR_TIMEOUT;
-    if (latency_ms) *latency_ms = j->latency_ms;
-    const epic_status st = j->status;
-    s->jobs.erase(it);
-    delete j;
+    ++j->waiters;  // the job outlives every waiter: the last one out of a released job frees it
+    const bool done =
+        s->done_cv.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] { return j->done; });
+    --j->waiters;
+    epic_status st = EPIC_ERR_TIMEOUT;
+    if (j->released) {
+        st = EPIC_ERR_NOT_FOUND;  // another waiter collected the ticket first
+    } else if (done) {
+        if (latency_ms) *latency_ms = j->latency_ms;
+        st = j->status;
+        s->jobs.erase(ticket);
+        j->released = true;
+    }
+    if (j->released && j->waiters == 0) delete j;
     return st;
 }
 
@@ -330,6 +373,8 @@ epic_status epic_server_destroy(epic_server_t s)
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (auto& m : s->slot_mem) epic::call_scratch_free(m);
+    cudaFreeHost(s->slot_flag);
     cudaFree(s->pool);
     for (auto& kv : s->jobs) delete kv.second;
     delete s;

@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
         L.epic_image.argtypes = [vp, vp, i, vp, vp, u]
         L.epic_image_host.argtypes = [vp, vp, i, vp, vp, u]
         L.epic_sync.argtypes = [vp]
+        L.epic_selftest_bounded_wait.argtypes = [vp, ctypes.c_longlong, vp]
         L.epic_kernel_times.argtypes = [vp, P(ctypes.c_char_p), P(ctypes.c_float), i, P(i)]
         L.epic_plan_get_info.argtypes = [vp, P(_PlanInfo)]
         L.epic_status_str.argtypes = [i]
@@ -296,6 +297,11 @@ class Plan:
 
     def sync(self):
         _check(self._lib, self._lib.epic_sync(self._handle()), self._h)
+
+    def selftest_bounded_wait(self, budget_cycles: int, stream=None):
+        """Launch the failure-detection self-test (a wait that runs out); see epic.h."""
+        _check(self._lib, self._lib.epic_selftest_bounded_wait(self._handle(), int(budget_cycles),
+                                                               _stream_handle(stream)), self._h)
 
     def kernel_times(self) -> List[Tuple[str, float]]:
         n = ctypes.c_int()

@@ -72,7 +72,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("field,value", [
     ("n_pol", 3), ("n_pol", 0), ("grid_n", 48), ("grid_n", 4), ("grid_n", 1024), ("max_time", 0),
     ("gcf_K", 0), ("gcf_K", 9), ("gcf_sigma_cells", 0.0), ("gcf_kind", 7), ("path", 9), ("n_chan", 0),
-    ("n_ant", 0), ("input_bits", 6), ("input_bits", 16), ("sub_int", -1), ("sub_int", 17)])
+    ("n_ant", 0), ("input_bits", 6), ("input_bits", 16), ("sub_int", -1), ("sub_int", 17), ("n_chan", 40000)])
 def test_invalid_descriptor_rejected_on_host(field, value):
     L = E.load()
     d, keep = _desc(**{field: value})

@@ -118,7 +118,8 @@ def test_full_workloads_sampled_channels(path, idx):
     cfg, v = _big(idx)
     got = run_gpu(cfg, v, path)
     chans = [0, cfg.n_chan // 2 + 1, cfg.n_chan - 1]
-    assert_parity(got[chans], oracle_image(cfg, v, chans=chans), path, cfg.name)
+    e = assert_parity(got[chans], oracle_image(cfg, v, chans=chans), path, cfg.name)
+    print(f"{path} {cfg.name} T={cfg.n_time}: max error / peak {e.max():.2e} (channels {chans})")
     assert np.all(np.isfinite(got))
     # XX and YY are sums of squares everywhere
     assert got[:, :2].min() >= -TOL[path] * got[:, :2].max()

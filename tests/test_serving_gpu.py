@@ -113,3 +113,38 @@ def test_server_argument_checks_on_host():
     d, lat = ctypes.c_int(), ctypes.c_double()
     assert L.epic_server_poll(None, 1, ctypes.byref(d), ctypes.byref(lat)) == 1
     assert L.epic_server_destroy(None) == 0
+
+
+# (station type of the streaming mix, channels per block): every type, including the
+# dual-pol 64-element 32 x 32 station and the 1024-element lattice, at its full block
+# length, with the mix's channel plan
+MIX_BLOCKS = [(0, 384), (1, 128), (2, 64), (3, 32)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("path", ["plain", "dftgemm"])
+def test_streaming_mix_station_types_match_oracle(path):
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    types = synth.mixed_station_types()
+    cfgs = [synth.serving_config(types[t], C) for t, C in MIX_BLOCKS]
+    plans = [E.Plan.from_config(cfg, path=path, max_time=cfg.n_time) for cfg in cfgs]
+    volts = [synth.make_voltages(cfg) for cfg in cfgs]
+    outs = [torch.empty((cfg.n_chan, cfg.n_prod, cfg.grid_n, cfg.grid_n), device="cuda") for cfg in cfgs]
+    torch.cuda.synchronize()
+    pool = 2 * max(v.nbytes for v in volts)
+    with E.Server(device_bytes=pool, slots=4) as srv:
+        tickets = []
+        for plan, v, o in zip(plans, volts, outs):
+            t = None
+            while t is None:
+                t = srv.submit(plan, v, o)
+            tickets.append(t)
+        for t in tickets:
+            srv.wait(t, timeout_ms=600000)
+    for cfg, v, o in zip(cfgs, volts, outs):
+        chans = [0, cfg.n_chan // 2, cfg.n_chan - 1]
+        e = assert_parity(o.cpu().numpy()[chans], oracle_image(cfg, v, chans=chans), path, cfg.name)
+        print(f"{path} {cfg.name} T={cfg.n_time}: max error / peak {e.max():.2e}")
+    for p in plans:
+        p.close()

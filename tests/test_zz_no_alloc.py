@@ -81,3 +81,24 @@ def test_static_scratch_rejects_formats_it_does_not_take():
             out = torch.zeros(plan.image_shape(cfg.n_time), device="cuda")
             st = f(plan._h, v.data_ptr(), cfg.n_time, torch.cuda.current_stream().cuda_stream, out.data_ptr(), 0)
             assert st == 7, L.epic_last_error(plan._h).decode()        # EPIC_ERR_UNSUPPORTED
+
+
+@pytest.mark.gpu
+def test_static_scratch_smallest_grid_many_samples():
+    # N = 8, one channel, one pol: 65,536 samples fit the array at once, more than one launch
+    # dimension takes, so the call runs in chunks; two calls in a row against epic_image
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    L, f = _entry()
+    cfg = synth.small_config(n_ant=6, n_chan=1, n_pol=1, grid_n=8, gcf_k=3, n_time=70000, seed=94, diameter_m=3.0)
+    with E.Plan.from_config(cfg, path="plain") as plan:
+        stream = torch.cuda.current_stream().cuda_stream
+        for call in range(2):
+            v = torch.from_numpy(synth.random_bytes((cfg.n_time, 1, 6, 1), seed=40 + call)).cuda()
+            ref = plan.image(v)
+            out = torch.full_like(ref, 3.0)
+            st = f(plan._h, v.data_ptr(), cfg.n_time, stream, out.data_ptr(), 0)
+            assert st == 0, L.epic_last_error(plan._h).decode()
+            torch.cuda.synchronize()
+            assert_parity(out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64), "plain",
+                          f"N=8 static-scratch call {call}")
