@@ -30,7 +30,8 @@
  *     centroid placed at cell (N/2, N/2).  Odd K: anchor = nearest cell (ties up),
  *     taps anchor +- (K-1)/2; even K: taps floor(u)-K/2+1 .. floor(u)+K/2.  No tap
  *     may leave the grid (EPIC_ERR_GRID_OVERFLOW at plan creation).
- *   - Both polarisations share one GCF (no polarisation mixing).
+ *   - Both polarisations share one GCF W; a per-element 2x2 polarisation-mixing
+ *     kernel may multiply it (epic_plan_desc.jones, Eq. 1's W_e^{ap}).
  *   - Device pointers must come from cudaMalloc (or torch) on the device that is
  *     current when the plan is created; host pointers are plain host memory.
  *   - Calls are stream-ordered and asynchronous unless stated; CUDA errors of
@@ -65,9 +66,14 @@ typedef enum {
                                    -> HBM -> square/accumulate kernel (the plain comparator)      */
     EPIC_PATH_FUSED_FP32 = 1,   /* one fused kernel per block: grid -> FP32 FFT -> products ->
                                    on-chip accumulation, images written once                      */
-    EPIC_PATH_DFTGEMM_FP16 = 2, /* fused kernel with the 2-D transform as two DFT-as-GEMM stages on
-                                   the tcgen05 tensor cores: FP16 operands, FP32 accumulation     */
-    EPIC_PATH_AUTO = 3          /* pick per plan (measured choice when a tuning entry exists)     */
+    EPIC_PATH_DFTGEMM_FP16 = 2, /* a gridding kernel writes FP16 grid tiles, then one tensor-core
+                                   kernel runs the 2-D transform as two DFT-as-GEMM stages on the
+                                   tcgen05 tensor cores (FP16 operands, FP32 accumulation), the
+                                   products and the accumulation; per (channel group, time chunk) */
+    EPIC_PATH_AUTO = 3          /* the DFT-as-GEMM path where the plan's occupied grid fits it,
+                                   else the plain FP32 path; epic_plan_tune then times every path
+                                   that takes the plan on the caller's block and keeps the
+                                   fastest (tuning parameter "path")                              */
 } epic_path;
 
 typedef enum {
@@ -210,6 +216,8 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  * as in epic_image; out is overwritten) for the candidate values of each of the
  * plan's tuning parameters in turn, keeping the fastest value of each, and leaves
  * the plan configured with them.  Parameters by path:
+ *   AUTO plans    path         0 plain FP32, 1 fused FP32, 2 DFT-as-GEMM (timed first; the chosen
+ *                              path's own parameters follow)
  *   PLAIN_FP32    chunk_mb     grid-buffer budget of one time chunk (MiB)
  *   FUSED_FP32    slab         image columns per work item
  *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a

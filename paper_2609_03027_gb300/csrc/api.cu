@@ -31,6 +31,8 @@ cudaError_t upload(T** dst, const T* src, size_t n, size_t* bytes)
     return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+void free_path_state(epic_plan_s* p);
+
 void free_plan(epic_plan_s* p)
 {
     if (!p) return;
@@ -48,11 +50,26 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->dt.w_taps);
     cudaFree(p->dt.jones);
     cudaFree(p->dt.dft_f16);
+    free_path_state(p);
+    cudaFree(p->tc.status);
+    cudaFree(p->stage_volt);
+    cudaFree(p->stage_out);
+    for (auto& ev : p->events) {
+        cudaEventDestroy(ev.start);
+        cudaEventDestroy(ev.stop);
+    }
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+// Everything a path owns: the tensor path's tables, the scratch, the recorded graph.
+void free_path_state(epic_plan_s* p)
+{
     cudaFree(p->tc.a1);
     cudaFree(p->tc.a2);
     cudaFree(p->tc.a1_off);
     cudaFree(p->tc.a2_off);
-    cudaFree(p->tc.status);
     cudaFree(p->tc.a2w);
     cudaFree(p->tc.a2w_off);
     cudaFree(p->tc.a1p);
@@ -66,20 +83,55 @@ void free_plan(epic_plan_s* p)
     cudaFree(p->tc.gell_off);
     cudaFree(p->tc.tbox);
     cudaFree(p->scratch);
-    cudaFree(p->stage_volt);
-    cudaFree(p->stage_out);
-    for (auto& ev : p->events) {
-        cudaEventDestroy(ev.start);
-        cudaEventDestroy(ev.stop);
-    }
+    int* status = p->tc.status;
+    p->tc = epic::TcState{};
+    p->tc.status = status;
+    p->scratch = nullptr;
+    p->scratch_bytes = 0;
+    p->chunk_budget = 0;
+    p->time_chunk = 0;
+    p->slab = 0;
+    p->fused_variant = 0;
+    p->dt.dft_bytes = 0;
+    p->tc_flops_per_sample = 0.0;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    cudaSetDevice(cur);
-    delete p;
+    p->gexec = nullptr;
+    p->g_T = -1;
 }
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+epic_status path_setup(epic_plan_s* p)
+{
+    switch (p->path) {
+        case EPIC_PATH_PLAIN_FP32: return epic::plain_setup(p);
+        case EPIC_PATH_FUSED_FP32: return epic::fused_setup(p);
+        case EPIC_PATH_DFTGEMM_FP16: return epic::dftgemm_setup(p);
+    }
+    return EPIC_ERR_INVALID_ARG;
+}
 }  // namespace
+
+namespace epic {
+epic_status set_path(epic_plan_s* p, int path)
+{
+    if (path == p->path) return EPIC_OK;
+    if (path != EPIC_PATH_PLAIN_FP32 && path != EPIC_PATH_FUSED_FP32 && path != EPIC_PATH_DFTGEMM_FP16)
+        return EPIC_ERR_UNSUPPORTED;
+    const int old = p->path;
+    cudaDeviceSynchronize();  // nothing of this plan may still run on the state freed here
+    free_path_state(p);
+    p->path = path;
+    epic_status st = path_setup(p);
+    if (st == EPIC_OK) return EPIC_OK;
+    const std::string why = p->last_error;
+    free_path_state(p);
+    p->path = old;
+    const epic_status back = path_setup(p);
+    p->last_error = why;
+    return back == EPIC_OK ? st : back;
+}
+}  // namespace epic
 
 namespace epic {
 
@@ -276,7 +328,8 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
     }
 
     int path = d->path;
-    if (path == EPIC_PATH_AUTO) path = EPIC_PATH_DFTGEMM_FP16;
+    p->auto_path = path == EPIC_PATH_AUTO;
+    if (path == EPIC_PATH_AUTO) path = EPIC_PATH_DFTGEMM_FP16;  // the tensor path where it can run
     p->path = path;
 
     // shared device tables
@@ -313,11 +366,11 @@ epic_status epic_plan_create(const epic_plan_desc* d, epic_plan_t* out)
         return st;
     }
 
-    switch (p->path) {
-        case EPIC_PATH_PLAIN_FP32: st = epic::plain_setup(p); break;
-        case EPIC_PATH_FUSED_FP32: st = epic::fused_setup(p); break;
-        case EPIC_PATH_DFTGEMM_FP16: st = epic::dftgemm_setup(p); break;
-        default: st = EPIC_ERR_INVALID_ARG;
+    st = path_setup(p);
+    if (st == EPIC_ERR_UNSUPPORTED && p->auto_path) {  // AUTO: the plain FP32 path takes every plan
+        free_path_state(p);
+        p->path = EPIC_PATH_PLAIN_FP32;
+        st = path_setup(p);
     }
     if (st != EPIC_OK) {
         set_create_error(p->last_error);

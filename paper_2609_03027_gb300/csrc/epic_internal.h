@@ -139,6 +139,7 @@ struct epic_plan_s {
     int smem_optin = 0;
     epic::TcState tc;                     // tensor-core path
     int fused_variant = 0;                // kernel variant chosen for fused paths
+    bool auto_path = false;               // created with EPIC_PATH_AUTO: the tuner may change path
     int slab = 0;                         // output columns per work item (fused paths)
 
     size_t chunk_budget = 0;              // scratch budget of one time chunk (chunked paths)
@@ -179,6 +180,9 @@ cudaError_t allow_max_smem(const void* fn, int optin);
 void ev_begin(epic_plan_s* p, const char* name, cudaStream_t s);
 void ev_end(epic_plan_s* p, cudaStream_t s);
 epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);
+// Switch the plan to another path (frees the current path's tables and scratch, sets up the
+// new one; on failure the plan is back on its previous path and the status is returned).
+epic_status set_path(epic_plan_s* p, int path);
 // one epic_image call after argument checks (flags without EPIC_GRAPH handling)
 epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags);
 // Grow c (zeroed on allocation) to what a call of p needs; allocates, so not on a hot path.

@@ -15,16 +15,18 @@
 //            A2 row ky       = [ Fr[:][ky] | Fi[:][ky] ]
 //            B2_p row kx     = [ Hr[:][kx] | -Hi[:][kx] ],  row 32+kx = [ Hi | Hr ]
 //   so that D2_p[ky][kx] = Re E_p, D2_p[ky][32+kx] = Im E_p.
-// Work item = (channel, block of 128 ky, slab of 32 kx); the XX, YY, Re/Im XY
-// sums of its 128 x 32 pixels stay in registers over every frame of a chunk.
+// A work item is (channel, block of 128 ky, slab of kx: 32 in the fallback kernels,
+// a pair of 32 in the warp-specialised ones); the XX, YY, Re/Im XY sums of its pixels
+// stay in registers over every frame of a chunk.
 //
-// Two kernels per (channel group, time chunk), stream-ordered, with the grid
-// tiles staying in L2 between them:
-//   k_dftgemm_grid  gather-grid every (t, c) frame of the chunk into an FP16
-//                   tile already in the UMMA K-major core-matrix layout
-//   k_dftgemm_mma   stage 1 -> TMEM -> FP16 shared B2 -> stage 2 -> TMEM ->
-//                   products -> register accumulation; images written (or
-//                   added) once per chunk
+// Two kernels per (channel group, time chunk), stream-ordered; the grid tiles of a
+// chunk go through HBM between them (up to 3 GB per chunk, far more than L2):
+//   k_dftgemm_grid_*  gather-grid every (t, c) frame of the chunk into FP16 tiles
+//                     already in the 128-byte swizzled UMMA K-major layout (tall
+//                     boxes: one such operand per row part)
+//   k_dftgemm_ws3     (or an older variant) stage 1 -> TMEM -> FP16 shared B2 ->
+//                     stage 2 -> TMEM -> products -> register accumulation; images
+//                     written (or added) once per chunk
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -2755,7 +2757,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e == cudaSuccess) e = cudaMalloc(&p->tc.tbox, (size_t)C * sizeof(int4));
     if (e == cudaSuccess)
         e = cudaMemcpy(p->tc.tbox, p->tc.tbox_h.data(), (size_t)C * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->tc.status, sizeof(int));
+    if (e == cudaSuccess && !p->tc.status) e = cudaMalloc(&p->tc.status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->tc.status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(p, e, "tensor path table upload");
     p->dt.dft_bytes = (n1 + n2 + n1p) * 2 + nw * 4 +

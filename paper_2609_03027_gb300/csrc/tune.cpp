@@ -23,12 +23,16 @@ epic_status set_fused_slab(epic_plan_s* p, int sw) { return epic::fused_set_slab
 epic_status set_dft_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_kernel(p, v); }
 epic_status set_dft_grid_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_grid_kernel(p, v); }
 epic_status set_dft_split(epic_plan_s* p, int v) { return epic::dftgemm_set_split(p, v); }
+epic_status set_path(epic_plan_s* p, int v) { return epic::set_path(p, v); }
 
 // the tuning parameters of a plan's path with their candidate and current values
 std::vector<Knob> knobs_for(const epic_plan_s* p)
 {
     std::vector<Knob> knobs;
     const int budget_mb = (int)(p->chunk_budget >> 20);
+    if (p->auto_path)  // EPIC_PATH_AUTO: the path itself, timed first (each path's own knobs follow)
+        knobs.push_back({"path", {EPIC_PATH_PLAIN_FP32, EPIC_PATH_FUSED_FP32, EPIC_PATH_DFTGEMM_FP16}, p->path,
+                         set_path});
     if (p->path == EPIC_PATH_PLAIN_FP32) {
         knobs.push_back({"chunk_mb", {128, 256, 512, 1024}, budget_mb, set_plain_chunk});
     } else if (p->path == EPIC_PATH_FUSED_FP32) {
@@ -100,6 +104,7 @@ extern "C" epic_status epic_plan_tune(epic_plan_t p, const uint8_t* volt, int T,
 
     drop_graph(p);
     std::vector<Knob> knobs = knobs_for(p);
+    const bool path_knob = p->auto_path;
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
@@ -137,6 +142,11 @@ extern "C" epic_status epic_plan_tune(epic_plan_t p, const uint8_t* volt, int T,
         epic_status sb = kb.set(p, best_v);
         if (st == EPIC_OK) st = sb;
         kb.current = best_v;
+        if (path_knob && k == 0) {  // the path is chosen: tune its own parameters next
+            std::vector<Knob> rest = knobs_for(p);
+            knobs.resize(1);
+            knobs.insert(knobs.end(), rest.begin() + 1, rest.end());
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

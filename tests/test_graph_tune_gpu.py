@@ -150,3 +150,38 @@ def test_plan_created_later_does_not_break_earlier_plan(path):
         ps.sync()
     assert_parity(ob, oracle_image(big, vb), path, "earlier plan")
     assert_parity(os_, oracle_image(small, vs), path, "later plan")
+
+
+def test_auto_path_tunes_the_path_and_keeps_parity():
+    # an AUTO plan starts on the tensor path; the tuner times every path that takes the plan
+    # and keeps the fastest, then tunes that path's own parameters
+    cfg = _cfg(seed=44)
+    vn = synth.make_voltages(cfg)
+    v = torch.from_numpy(vn).cuda()
+    ref = oracle_image(cfg, vn)
+    with E.Plan.from_config(cfg, path="auto") as plan:
+        assert plan.info()["path_name"] == "dftgemm"
+        rep = plan.tune(v, reps=1)
+        assert "path" in rep["params"] and rep["params"]["path"] == plan.info()["path"]
+        got = plan.image(v).cpu().numpy()
+        plan.sync()
+        assert_parity(got, ref, plan.info()["path_name"], "auto after tuning")
+        for name, path in (("plain", 0), ("fused", 1), ("dftgemm", 2)):   # each path on demand
+            plan.set_param("path", path)
+            assert plan.get_param("path") == path and plan.info()["path_name"] == name
+            assert_parity(plan.image(v).cpu().numpy(), ref, name, f"auto plan set to {name}")
+
+
+def test_auto_path_takes_a_grid_the_tensor_path_refuses():
+    # 20,000 dual-pol elements on a 512 x 512 grid: the occupied box is too tall for the
+    # tensor-core kernels, so an AUTO plan lands on the plain FP32 path and images correctly
+    cfg = synth.config(6)
+    cfg.n_time = 2
+    vn = synth.make_voltages(cfg)
+    with E.Plan.from_config(cfg, path="auto", max_time=2) as plan:
+        assert plan.info()["path_name"] == "plain"
+        got = plan.image(torch.from_numpy(vn).cuda()).cpu().numpy()
+        plan.sync()
+        rep = plan.tune(torch.from_numpy(vn).cuda(), reps=1)
+        assert rep["params"]["path"] in (0, 1)
+    assert_parity(got, oracle_image(cfg, vn), "plain", cfg.name)
