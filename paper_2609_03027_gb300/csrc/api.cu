@@ -82,6 +82,10 @@ void free_path_state(epic_plan_s* p)
     cudaFree(p->tc.gell_w);
     cudaFree(p->tc.gell_off);
     cudaFree(p->tc.tbox);
+    cudaFree(p->tc.pl_ptr);
+    cudaFree(p->tc.pl_off);
+    cudaFree(p->tc.pl_e);
+    cudaFree(p->tc.pl_w);
     cudaFree(p->scratch);
     int* status = p->tc.status;
     p->tc = epic::TcState{};

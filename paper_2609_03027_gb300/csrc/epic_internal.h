@@ -54,7 +54,11 @@ struct TcState {
     int grid_blocks = 0;           // blocks of the persistent gridding kernel
     int grid_max_cells = 0;        // largest occupied box (cells)
     int grid_max_list = 0;         // (cell, element) entries per channel
-    int grid_variant = 1;          // 1: persistent row-major gather, 2: balanced task lists
+    int grid_variant = 1;          // 1: persistent row-major gather, 2: balanced task lists, 3: pair lists
+    int* pl_ptr = nullptr;         // pair-list gridding: per channel entry offsets of the box's cell
+    int* pl_off = nullptr;         //   pairs (row-major) and where each channel's start
+    int* pl_e = nullptr;           //   entries: element
+    float2* pl_w = nullptr;        //   entries: weights at x and x + 1
     int4* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list

@@ -806,6 +806,193 @@ __global__ void __launch_bounds__(kGridBalBlock, 1) k_dftgemm_grid_bal(GridBalAr
     }
 }
 
+// Row-major pair-list gridding kernel (real GCF weights): persistent like
+// k_dftgemm_grid_ps, but a task's list is that of a run of two horizontally adjacent
+// cells (every element reaching either cell, one weight per cell), so each voltage
+// read serves both cells, and the lists are read through L1 instead of being staged in
+// shared memory -- only the pass's voltages are, so boxes of any size fit.  Every cell
+// pair of the box (row parts padded, no entries for those rows) is a task, so each
+// pass writes every tile byte but the K padding (zero from the buffer's first use).
+// Threads take consecutive cell pairs of a row: a warp's stores fill whole 128-byte
+// rows of the swizzled tile.  With H the unpacked voltages are FP16 pairs, the F frames
+// of an element side by side (exact for 4- and 8-bit samples), so one 16-byte load
+// serves two frames.
+constexpr int kGridPlThreads = 512;
+
+struct GridPlArgs {
+    GridArgs g;
+    const int* pl_ptr;    // per channel: entry offsets of the box's cell pairs, row-major, + 1
+    const int* pl_off;    // [C] start of channel c's offsets in pl_ptr
+    const int* pl_e;      // entries: element
+    const float2* pl_w;   // entries: weights at cells x and x + 1
+};
+
+__host__ __device__ inline size_t grid_pl_smem(int F, int A, int frame_bytes, bool H)
+{
+    const size_t ap = (size_t)((frame_bytes + 15) & ~15);
+    return 2ull * F * ap + (H ? 8ull : 16ull) * F * A;
+}
+
+template <int F, bool H>
+__global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs pa)
+{
+    const GridArgs& a = pa.g;
+    extern __shared__ __align__(128) uint8_t gsm[];
+    __shared__ uint64_t bar_raw[2];
+    const int tid = threadIdx.x;
+    const int A = a.A, P = a.P, AP = A * P * (a.bits / 4);  // bytes of one frame
+    const int APr = (AP + 15) & ~15;
+    uint8_t* raw = gsm;                                          // [2][F][APr]
+    float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);   // [F][A] (FP32) or [A][F] (H)
+    uint2* svh = reinterpret_cast<uint2*>(sv);
+
+    const long long W = (long long)a.n_ch * a.nt;
+    const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+    if (tid == 0) {
+        tc::mbar_init(&bar_raw[0], 1);
+        tc::mbar_init(&bar_raw[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < F * A; i += blockDim.x) {  // short passes read all F frames: start them at zero
+        if (H) svh[i] = make_uint2(0u, 0u);  // 8 bytes per (element, frame): the buffer holds F A of them
+        else sv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (w0 >= w1) return;
+
+    auto pass_len = [&](long long w) {
+        const int f = (int)(w % a.nt);
+        return (int)min((long long)min(F, a.nt - f), w1 - w);
+    };
+    auto fetch = [&](long long w, int b) {  // thread 0: raw bytes of the pass starting at w -> buffer b
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        tc::mbar_expect_tx(&bar_raw[b], (uint32_t)(nf * AP));
+        for (int i = 0; i < nf; ++i)
+            tc::bulk_g2s(raw + (size_t)(b * F + i) * APr,
+                         a.volt + ((size_t)(a.t0 + f + i) * a.C + a.c0 + cl) * (size_t)AP, (uint32_t)AP, &bar_raw[b]);
+    };
+
+    uint32_t ph = 0, pending = 0;
+    int buf = 0;
+    bool ok = true;
+    if (a.bulk && tid == 0) {
+        fetch(w0, 0);
+        pending = 1u;
+    }
+    for (long long w = w0; w < w1;) {
+        const int cl = (int)(w / a.nt), f = (int)(w % a.nt), nf = pass_len(w);
+        const long long wn = w + nf;
+        const int c = a.c0 + cl;
+        const int4 b = a.box[c];
+        const int nxp = b.z, nyp = b.w;
+        const int4 tp = a.tbox[c];
+        const int nyh = tp.x, N1h = P * nyh;
+        const uint32_t part_bytes = (uint32_t)N1h * pad64(2 * nxp) * 2;
+        const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
+        if (a.bulk && tid == 0 && wn < w1) {  // the other buffer was consumed by the previous pass
+            fetch(wn, buf ^ 1);
+            pending |= 1u << (buf ^ 1);
+        }
+        if (a.bulk) {
+            const bool got = tc::mbar_wait(&bar_raw[buf], (ph >> buf) & 1u, kWaitBudget);
+            if (got) {
+                ph ^= 1u << buf;
+                pending &= ~(1u << buf);
+            }
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+        }
+        for (int i = tid; i < nf * A; i += blockDim.x) {
+            const int fi = i / A, e = i - fi * A;
+            const uint8_t* fr = a.bulk ? raw + (size_t)(buf * F + fi) * APr
+                                       : a.volt + ((size_t)(a.t0 + f + fi) * a.C + c) * (size_t)AP;
+            const float4 q = load_quad(fr, e, P, a.bits, jm);
+            if (H) svh[e * F + fi] = make_uint2(pack_h2(q.x, q.y), pack_h2(q.z, q.w));
+            else sv[fi * A + e] = q;
+        }
+        __syncthreads();
+        const int half = nxp >> 1;
+        const int tasks = tp.z * half;
+        const int* ptr_c = pa.pl_ptr + pa.pl_off[c];
+        for (int task = tid; task < tasks; task += blockDim.x) {
+            const int y = task / half, x = 2 * (task - y * half);
+            float4 g[2][F];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) g[j][fi] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int k1 = y < nyp ? __ldg(ptr_c + task + 1) : 0;
+            for (int k = y < nyp ? __ldg(ptr_c + task) : 0; k < k1; ++k) {
+                const int e = __ldg(pa.pl_e + k);
+                const float2 wv = __ldg(pa.pl_w + k);
+                float4 v[F];
+                if constexpr (H) {
+                    uint2 hv[F];
+                    if constexpr (F == 1) {
+                        hv[0] = svh[e];
+                    } else {
+                        const uint4* q = reinterpret_cast<const uint4*>(svh + e * F);
+#pragma unroll
+                        for (int jj = 0; jj < F / 2; ++jj) {
+                            const uint4 u = q[jj];
+                            hv[2 * jj] = make_uint2(u.x, u.y);
+                            hv[2 * jj + 1] = make_uint2(u.z, u.w);
+                        }
+                    }
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) {
+                        const float2 xx = __half22float2(*reinterpret_cast<const __half2*>(&hv[fi].x));
+                        const float2 yy = __half22float2(*reinterpret_cast<const __half2*>(&hv[fi].y));
+                        v[fi] = make_float4(xx.x, xx.y, yy.x, yy.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + e];
+                }
+#pragma unroll
+                for (int fi = 0; fi < F; ++fi) {
+                    g[0][fi].x = fmaf(wv.x, v[fi].x, g[0][fi].x);
+                    g[0][fi].y = fmaf(wv.x, v[fi].y, g[0][fi].y);
+                    g[0][fi].z = fmaf(wv.x, v[fi].z, g[0][fi].z);
+                    g[0][fi].w = fmaf(wv.x, v[fi].w, g[0][fi].w);
+                    g[1][fi].x = fmaf(wv.y, v[fi].x, g[1][fi].x);
+                    g[1][fi].y = fmaf(wv.y, v[fi].y, g[1][fi].y);
+                    g[1][fi].z = fmaf(wv.y, v[fi].z, g[1][fi].z);
+                    g[1][fi].w = fmaf(wv.y, v[fi].w, g[1][fi].w);
+                }
+            }
+            const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
+            const int hpart = y / nyh, R0 = y - hpart * nyh;
+#pragma unroll
+            for (int fi = 0; fi < F; ++fi) {
+                if (fi >= nf) break;
+                uint8_t* tile =
+                    a.tiles + ((size_t)(f + fi) * a.n_ch + cl) * a.tile_stride + (size_t)hpart * part_bytes;
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_re, N1h) + within) = pack_h2(g[0][fi].x, g[1][fi].x);
+                *reinterpret_cast<uint32_t*>(tile + sw_chunk(R0, kc_im, N1h) + within) = pack_h2(g[0][fi].y, g[1][fi].y);
+                if (P == 2) {
+                    const int R1 = nyh + R0;
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_re, N1h) + within) =
+                        pack_h2(g[0][fi].z, g[1][fi].z);
+                    *reinterpret_cast<uint32_t*>(tile + sw_chunk(R1, kc_im, N1h) + within) =
+                        pack_h2(g[0][fi].w, g[1][fi].w);
+                }
+            }
+        }
+        __syncthreads();  // the voltages are reused by the next pass
+        w = wn;
+        buf ^= 1;
+    }
+    if (!ok && tid == 0) {
+        // leave no bulk copy in flight into this block's shared memory
+        for (int b2 = 0; b2 < 2; ++b2)
+            if ((pending >> b2) & 1u) tc::mbar_wait(&bar_raw[b2], (ph >> b2) & 1u, kWaitBudget);
+        atomicExch(a.status, 1);
+    }
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -2428,11 +2615,40 @@ epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget)
 
 static epic_status grid_bal_config(epic_plan_s* p, int F);
 
+// Frames per pass and grid size of the pair-list gridding kernel (UNSUPPORTED when F
+// frames of voltages do not fit in shared memory).
+static epic_status grid_pl_config(epic_plan_s* p, int F)
+{
+    if (!p->tc.pl_ptr || (F != 1 && F != 2 && F != 4 && F != 8)) return EPIC_ERR_UNSUPPORTED;
+    const bool H = p->jones.empty();  // FP16-pair voltages unless polarisation mixing
+    const size_t bytes = grid_pl_smem(F, p->A, p->A * p->P * (p->bits / 4), H);
+    const void* fn = nullptr;
+    if (H) fn = F == 8 ? (const void*)k_dftgemm_grid_pl<8, true> : F == 4 ? (const void*)k_dftgemm_grid_pl<4, true>
+              : F == 2 ? (const void*)k_dftgemm_grid_pl<2, true> : (const void*)k_dftgemm_grid_pl<1, true>;
+    else fn = F == 8 ? (const void*)k_dftgemm_grid_pl<8, false> : F == 4 ? (const void*)k_dftgemm_grid_pl<4, false>
+              : F == 2 ? (const void*)k_dftgemm_grid_pl<2, false> : (const void*)k_dftgemm_grid_pl<1, false>;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_pl)");
+    if (bytes + fa.sharedSizeBytes > (size_t)p->smem_optin) return EPIC_ERR_UNSUPPORTED;
+    e = allow_max_smem(fn, p->smem_optin);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid_pl)");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGridPlThreads, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_dftgemm_grid_pl)");
+    if (occ < 1) return EPIC_ERR_UNSUPPORTED;
+    p->tc.grid_frames = F;
+    p->tc.grid_smem = (int)bytes;
+    p->tc.grid_blocks = p->sm_count * occ;
+    return EPIC_OK;
+}
+
 // Frames per pass of the persistent gridding kernel and its grid size (the blocks
 // that fit on the GPU at once).  UNSUPPORTED when F frames do not fit in shared memory.
 epic_status dftgemm_grid_config(epic_plan_s* p, int F)
 {
     if (p->tc.grid_variant == 2) return grid_bal_config(p, F);
+    if (p->tc.grid_variant == 3) return grid_pl_config(p, F);
     if (F != 1 && F != 2 && F != 4 && F != 8) return EPIC_ERR_UNSUPPORTED;
     const size_t bytes =
         grid_ps_smem(F, p->A, p->A * p->P * (p->bits / 4), p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
@@ -2489,12 +2705,14 @@ static epic_status grid_bal_config(epic_plan_s* p, int F)
     return EPIC_OK;
 }
 
-// Gridding kernel variant: 1 = persistent row-major gather, 2 = balanced task lists.
-// Keeps the frames per pass if the variant allows them, else the largest it allows.
+// Gridding kernel variant: 1 = persistent row-major gather, 2 = balanced task lists,
+// 3 = row-major pair lists.  Keeps the frames per pass if the variant allows them, else
+// the largest it allows.
 epic_status dftgemm_set_grid_kernel(epic_plan_s* p, int variant)
 {
-    if (variant != 1 && variant != 2) return EPIC_ERR_UNSUPPORTED;
+    if (variant < 1 || variant > 3) return EPIC_ERR_UNSUPPORTED;
     if (variant == 2 && !p->tc.gtask) return EPIC_ERR_UNSUPPORTED;
+    if (variant == 3 && !p->tc.pl_ptr) return EPIC_ERR_UNSUPPORTED;
     if (variant == 1 && !p->tc.grid_ps) return EPIC_ERR_UNSUPPORTED;
     const int old_variant = p->tc.grid_variant, old_f = p->tc.grid_frames;
     p->tc.grid_variant = variant;
@@ -2815,6 +3033,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
         std::vector<int> toff(C + 1, 0), eoff(C + 1, 0);
         std::vector<TaskW> pw;  // weights of the channel's run lists
         std::vector<int2> ord;
+        std::vector<int> pl_ptr, pl_off(C), pl_e;  // the same lists row-major (pair-list kernel)
+        std::vector<TaskW> pl_w;
         bool fits = true;
         int tmax = 0, emax = 0;
         for (int c = 0; c < C && fits; ++c) {
@@ -2845,6 +3065,15 @@ epic_status dftgemm_setup(epic_plan_s* p)
                         L.push_back(make_int2(el, (int)pw.size()));
                     }
                 }
+            pl_off[c] = (int)pl_ptr.size();
+            for (const std::vector<int2>& L : plist) {
+                pl_ptr.push_back((int)pl_e.size());
+                for (const int2& en : L) {
+                    pl_e.push_back(en.x);
+                    pl_w.push_back(pw[en.y - 1]);
+                }
+            }
+            pl_ptr.push_back((int)pl_e.size());
             std::vector<int> idx;
             for (int q = 0; q < hp * bx.ny; ++q)
                 if (!plist[q].empty()) idx.push_back(q);
@@ -2913,6 +3142,22 @@ epic_status dftgemm_setup(epic_plan_s* p)
         }
         toff[C] = (int)tasks.size();
         eoff[C] = (int)ell_e.size();
+        if (kTaskCells == 2 && !pl_e.empty() && pl_e.size() < (1u << 31)) {  // pair lists for k_dftgemm_grid_pl
+            e = cudaMalloc(&p->tc.pl_ptr, pl_ptr.size() * sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->tc.pl_ptr, pl_ptr.data(), pl_ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.pl_off, pl_off.size() * sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->tc.pl_off, pl_off.data(), pl_off.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.pl_e, pl_e.size() * sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->tc.pl_e, pl_e.data(), pl_e.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&p->tc.pl_w, pl_w.size() * sizeof(float2));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->tc.pl_w, pl_w.data(), pl_w.size() * sizeof(float2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(p, e, "pair-list upload");
+            p->dt.dft_bytes += (pl_ptr.size() + pl_off.size() + pl_e.size()) * sizeof(int) + pl_w.size() * sizeof(float2);
+        }
         if (fits && !tasks.empty()) {
             e = cudaMalloc(&p->tc.gtask, tasks.size() * sizeof(int4));
             if (e == cudaSuccess) e = cudaMemcpy(p->tc.gtask, tasks.data(), tasks.size() * sizeof(int4),
@@ -2936,7 +3181,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
             p->tc.grid_variant = 2;
             epic_status bst = EPIC_ERR_UNSUPPORTED;
             for (int gf = 2; gf >= 1 && bst == EPIC_ERR_UNSUPPORTED; gf >>= 1) bst = grid_bal_config(p, gf);
-            if (bst != EPIC_OK) {  // the balanced kernel does not fit: keep the row-major one
+            if (bst != EPIC_OK) {  // the balanced kernel does not fit: the pair-list one, else row-major
                 if (bst != EPIC_ERR_UNSUPPORTED) return bst;
                 p->tc.grid_variant = 1;
                 cudaFree(p->tc.gtask);
@@ -2953,6 +3198,19 @@ epic_status dftgemm_setup(epic_plan_s* p)
                 if (p->tc.grid_ps) {
                     const epic_status kst = dftgemm_grid_config(p, keep_f);
                     if (kst != EPIC_OK) return kst;
+                }
+                if (p->tc.pl_ptr) {
+                    p->tc.grid_variant = 3;
+                    epic_status pst = EPIC_ERR_UNSUPPORTED;
+                    for (int gf = 4; gf >= 1 && pst == EPIC_ERR_UNSUPPORTED; gf >>= 1) pst = grid_pl_config(p, gf);
+                    if (pst != EPIC_OK) {
+                        if (pst != EPIC_ERR_UNSUPPORTED) return pst;
+                        p->tc.grid_variant = 1;
+                        if (p->tc.grid_ps) {
+                            const epic_status kst = dftgemm_grid_config(p, keep_f);
+                            if (kst != EPIC_OK) return kst;
+                        }
+                    }
                 }
             } else {
                 p->dt.dft_bytes += tasks.size() * sizeof(int4) + ell_e.size() * (sizeof(int) + sizeof(TaskW)) +
@@ -3061,7 +3319,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
-            if (p->tc.grid_ps || p->tc.grid_variant == 2) {
+            if (p->tc.grid_ps || p->tc.grid_variant >= 2) {
                 GridArgs g{};
                 g.volt = volt;
                 g.t0 = t0;
@@ -3087,7 +3345,26 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                 g.bulk = ((A * P * (p->bits / 4)) % 16 == 0 && ((uintptr_t)volt & 15) == 0) ? 1 : 0;
                 const int gb = (int)std::min<long long>(p->tc.grid_blocks, (long long)ng * nt);
                 ev_begin(p, "k_dftgemm_grid", s);
-                if (p->tc.grid_variant == 2) {
+                if (p->tc.grid_variant == 3) {
+                    GridPlArgs pa{};
+                    pa.g = g;
+                    pa.pl_ptr = p->tc.pl_ptr;
+                    pa.pl_off = p->tc.pl_off;
+                    pa.pl_e = p->tc.pl_e;
+                    pa.pl_w = reinterpret_cast<const float2*>(p->tc.pl_w);
+                    const size_t sm = p->tc.grid_smem;
+                    if (p->jones.empty()) {
+                        if (F == 8) k_dftgemm_grid_pl<8, true><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else if (F == 4) k_dftgemm_grid_pl<4, true><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else if (F == 2) k_dftgemm_grid_pl<2, true><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else k_dftgemm_grid_pl<1, true><<<gb, kGridPlThreads, sm, s>>>(pa);
+                    } else {
+                        if (F == 8) k_dftgemm_grid_pl<8, false><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else if (F == 4) k_dftgemm_grid_pl<4, false><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else if (F == 2) k_dftgemm_grid_pl<2, false><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        else k_dftgemm_grid_pl<1, false><<<gb, kGridPlThreads, sm, s>>>(pa);
+                    }
+                } else if (p->tc.grid_variant == 2) {
                     GridBalArgs ba{};
                     ba.g = g;
                     ba.tasks = p->tc.gtask;

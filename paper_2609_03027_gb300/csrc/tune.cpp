@@ -42,9 +42,9 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
             knobs.push_back({"mma_kernel", {1, 2, 3}, p->tc.ws_variant, set_dft_kernel});
             knobs.push_back({"split", {-1, 0, 1}, p->tc.split, set_dft_split});
         }
-        if (p->tc.grid_ps && p->tc.gtask)
-            knobs.push_back({"grid_kernel", {1, 2}, p->tc.grid_variant, set_dft_grid_kernel});
-        if (p->tc.grid_ps || p->tc.gtask)
+        if ((p->tc.grid_ps ? 1 : 0) + (p->tc.gtask ? 1 : 0) + (p->tc.pl_ptr ? 1 : 0) >= 2)
+            knobs.push_back({"grid_kernel", {1, 2, 3}, p->tc.grid_variant, set_dft_grid_kernel});
+        if (p->tc.grid_ps || p->tc.gtask || p->tc.pl_ptr)
             knobs.push_back({"grid_frames", {1, 2, 4, 8}, p->tc.grid_frames, set_dft_frames});
         knobs.push_back({"chunk_mb", {96, 192, 384, 768, 1536, 3072}, budget_mb, set_dft_chunk});
     }

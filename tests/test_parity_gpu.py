@@ -305,3 +305,42 @@ def test_tall_boxes_in_row_parts(case, split):
             assert_parity(got[k], ref[k], "dftgemm", f"{case} set {k}")
     else:
         assert_parity(got, ref, "dftgemm", case)
+
+
+@pytest.mark.parametrize("grid_kernel", [1, 2, 3])
+@pytest.mark.parametrize("case", ["dual-pol", "single-pol", "dual-pol-8bit-mixed", "small"])
+def test_every_gridding_kernel_matches_oracle(case, grid_kernel):
+    # the tensor path's gridding kernels (row-major cell lists, balanced task lists, row-major
+    # pair lists) each write the tiles the transform reads; any of them gives oracle images
+    if case == "small":
+        cfg = synth.small_config(n_ant=40, n_chan=3, n_pol=2, grid_n=64, gcf_k=5, n_time=9, seed=77, diameter_m=16.0)
+        T, A, C, P = 9, 40, 3, 2
+    else:
+        A, C, P, N, K, T, diam, extra = TALL[case]
+        cfg = synth.small_config(n_ant=A, n_chan=C, n_pol=P, grid_n=N, gcf_k=K, n_time=T, seed=500 + A,
+                                 diameter_m=diam, sigma=0.7)
+        cfg = dataclasses.replace(cfg, input_bits=extra.get("bits", 4))
+        if extra.get("jones"):
+            cfg = dataclasses.replace(cfg, jones=synth.make_jones(cfg, seed=9, gain_rms=0.2, leak_rms=0.2))
+    v = synth.random_bytes((T, C, A, P) + ((2,) if cfg.input_bits == 8 else ()), seed=A + 3 * T)
+    ref = oracle_image(cfg, v)
+    with E.Plan.from_config(cfg, path="dftgemm", max_time=T) as plan:
+        try:
+            plan.set_param("grid_kernel", grid_kernel)
+        except E.EpicError as ex:
+            assert "UNSUPPORTED" in str(ex)
+            pytest.skip(f"gridding kernel {grid_kernel} does not take this plan")
+        for F in (1, 2, 4, 8):
+            try:
+                plan.set_param("grid_frames", F)
+            except E.EpicError:
+                continue
+            got = plan.image(torch.from_numpy(v).cuda()).cpu().numpy()
+            plan.sync()
+            assert_parity(got, ref, "dftgemm", f"{case} grid_kernel={grid_kernel} F={F}")
+
+
+def test_pair_list_gridding_is_the_default_where_the_balanced_kernel_does_not_fit():
+    cfg = synth.config(3).subset([383], n_time=4)   # the tallest SKA-Low channel
+    with E.Plan.from_config(cfg, path="dftgemm", max_time=4) as plan:
+        assert plan.get_param("grid_kernel") == 3
