@@ -135,6 +135,7 @@ struct MmaArgs {
     int C;                      // channels of the plan (image sets are [C][nprod][N][N])
     const int4* tbox;           // k_dftgemm_ws3: per channel row parts (nyh, H, H nyh, 0)
     int nbt;                    // k_dftgemm_ws3: tile-part buffers in shared memory (2..4)
+    const long long* wcum;      // k_dftgemm_ws3<1>: [C + 1] prefix sums of the channels' item costs per frame
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -171,6 +172,28 @@ __device__ __forceinline__ void store_pixels16(float* op, int nk, int accumulate
         for (int i = 0; i < 16; ++i)
             if (i < nk) op[i] = (accumulate ? op[i] : 0.f) + v[i];
     }
+}
+
+// First unit of block b of G when a launch's units -- ipc items of each of n_ch channels from
+// c0 in channel order, nt frames per item, item-major -- are cut into G ranges of equal cost,
+// a unit costing its channel's weight (wcum: prefix sums of the weights over the plan's
+// channels).  Without weights, G ranges of equal numbers of units.  Non-decreasing in b,
+// 0 at b = 0 and every unit at b = G.
+__device__ __forceinline__ long long split_start(const long long* wcum, int c0, int n_ch, int ipc, int nt, int b, int G)
+{
+    const long long per = (long long)ipc * nt;  // units of one channel
+    if (!wcum) return (long long)n_ch * per * b / G;
+    const long long base = wcum[c0];
+    const long long s = per * (wcum[c0 + n_ch] - base) * b / G;  // cost position of the block's start
+    int lo = 0, hi = n_ch;                                        // last channel whose units start at or before s
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (per * (wcum[c0 + mid] - base) <= s) lo = mid;
+        else hi = mid;
+    }
+    const long long w = wcum[c0 + lo + 1] - wcum[c0 + lo];
+    const long long u = min(per, (s - per * (wcum[c0 + lo] - base)) / w);
+    return (long long)lo * per + u;
 }
 
 // Unpack and gather-grid frames of one chunk into FP16 UMMA tiles.  A block
@@ -335,8 +358,9 @@ __global__ void __launch_bounds__(kThreads) k_dftgemm_grid_ps(GridArgs a)
     int* cone = reinterpret_cast<int*>(con);                             // complex: e ...
     float2* conw = reinterpret_cast<float2*>(cone + ((a.max_list + 1) & ~1));  // ... and w
 
-    const long long W = (long long)a.n_ch * a.nt;
-    const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+    // (channel, frame) pairs [w0, w1) of this block
+    const long long w0 = split_start(nullptr, a.c0, a.n_ch, 1, a.nt, blockIdx.x, gridDim.x);
+    const long long w1 = split_start(nullptr, a.c0, a.n_ch, 1, a.nt, blockIdx.x + 1, gridDim.x);
     if (tid == 0) {
         tc::mbar_init(&bar_raw[0], 1);
         tc::mbar_init(&bar_raw[1], 1);
@@ -846,8 +870,9 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
     float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);   // [F][A] (FP32) or [A][F] (H)
     uint2* svh = reinterpret_cast<uint2*>(sv);
 
-    const long long W = (long long)a.n_ch * a.nt;
-    const long long w0 = W * blockIdx.x / gridDim.x, w1 = W * (blockIdx.x + 1) / gridDim.x;
+    // (channel, frame) pairs [w0, w1) of this block
+    const long long w0 = split_start(nullptr, a.c0, a.n_ch, 1, a.nt, blockIdx.x, gridDim.x);
+    const long long w1 = split_start(nullptr, a.c0, a.n_ch, 1, a.nt, blockIdx.x + 1, gridDim.x);
     if (tid == 0) {
         tc::mbar_init(&bar_raw[0], 1);
         tc::mbar_init(&bar_raw[1], 1);
@@ -2163,18 +2188,23 @@ __device__ __noinline__ void ws3_split_finish(const MmaArgs& a, int item, int c,
     asm volatile("bar.sync 3, 512;" ::: "memory");
     if (tid == 0) {
         const long long s0 = (long long)item * a.nt, s1 = s0 + a.nt - 1;
-        const long long G = gridDim.x;
-        auto owner = [&](long long f) {  // block whose range [U b / G, U (b + 1) / G) holds f
-            long long b = f * G / U;
-            while (b + 1 < G && U * (b + 1) / G <= f) ++b;
-            while (b > 0 && U * b / G > f) --b;
-            return (int)b;
+        const int G = gridDim.x, ipc = a.n_kb * a.n_g;
+        auto start = [&](int b) { return split_start(a.wcum, a.c0, a.n_ch, ipc, a.nt, b, G); };
+        auto owner = [&](long long f) {  // the block whose range [start(b), start(b + 1)) holds f
+            int lo = 0, hi = G;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (start(mid) <= f) lo = mid;
+                else hi = mid;
+            }
+            return lo;
         };
+        (void)U;
         int n = 0;
         const int b1 = owner(s1);
         for (int b = owner(s0); b <= b1; ++b) {
-            const long long bw0 = U * b / G;
-            if (bw0 == U * (b + 1) / G) continue;  // no frames: no part
+            const long long bw0 = start(b);
+            if (bw0 == start(b + 1)) continue;  // no frames: no part
             split_slot[n++] = 2 * b + (s0 <= bw0 ? 0 : 1);
         }
         const bool last = atomicAdd(&a.counters[item], 1) == n - 1;
@@ -2250,7 +2280,9 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
     // item-major order (equal shares; items cut at share boundaries are summed by the
     // block that stores their last part); else whole items blockIdx.x, + gridDim.x, ...
     const long long U = (long long)items * a.nt;
-    const long long wb0 = U * blockIdx.x / gridDim.x, wb1 = U * (blockIdx.x + 1) / gridDim.x;
+    const int ipc = a.n_kb * a.n_g;  // items per channel
+    const long long wb0 = split_start(a.wcum, a.c0, a.n_ch, ipc, a.nt, blockIdx.x, gridDim.x);
+    const long long wb1 = split_start(a.wcum, a.c0, a.n_ch, ipc, a.nt, blockIdx.x + 1, gridDim.x);
 
     if (warp >= 16) {
         // ------------------------------------------------------------ control warpgroup
@@ -2981,6 +3013,20 @@ epic_status dftgemm_setup(epic_plan_s* p)
     p->dt.dft_bytes = (n1 + n2 + n1p) * 2 + nw * 4 +
                       (a1_off.size() + a2_off.size() + a1p_off.size() + a2w_off.size()) * sizeof(long long);
 
+    // Work split weights of k_dftgemm_ws3's equal shares, per frame of a channel's work item:
+    // a fixed epilogue 2, an epilogue 1 per row part and stage-2 work in proportion to the rows
+    // (about 1000 + 1200 H + 10 H nyh SM cycles, from clock64 timelines of the kernel).
+    {
+        std::vector<long long> wc(C + 1, 0);
+        for (int c = 0; c < C; ++c) {
+            const int4 r = p->tc.tbox_h[c];
+            wc[c + 1] = wc[c] + 1000 + 1200LL * r.y + 10LL * r.z;
+        }
+        cudaError_t ew = cudaMalloc(&p->tc.wcum, (C + 1) * sizeof(long long));
+        if (ew == cudaSuccess) ew = cudaMemcpy(p->tc.wcum, wc.data(), (C + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+        if (ew != cudaSuccess) return cuda_fail(p, ew, "work-split weights upload");
+    }
+
     // algorithmic work of the pruned DFT-as-GEMM per time sample (all channels, pols):
     // complex MACs  nyp*nxp*N (rows along x) + N*nyp*N (columns along y), 8 flops each
     double fl = 0.0;
@@ -3229,7 +3275,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
         while (gf > 1 && sizeof(float4) * (size_t)gf * p->A > gl) gf >>= 1;
         sv_bytes = sizeof(float4) * (size_t)gf * p->A;
     }
-    if (!p->tc.grid_ps) {
+    if (!p->tc.grid_ps && p->tc.grid_variant == 1) {  // only the gather kernel is left: its frames and memory
         p->tc.grid_frames = gf;
         p->tc.grid_smem = (int)(sv_bytes + (p->tc.grid_csr_smem ? csr_bytes : 0));
         if (p->tc.grid_smem > p->smem_optin) {
@@ -3312,6 +3358,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     a.a1p_off = p->tc.a1p_off;
     a.tbox = p->tc.tbox;
     a.nbt = p->tc.nbt;
+    a.wcum = p->tc.wcum;
     const int fpc = kGridFramesPerBlock;
     const int F = p->tc.grid_frames;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
@@ -3320,6 +3367,16 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
             if (p->tc.grid_ps || p->tc.grid_variant >= 2) {
+                // the launch's shared memory must be the chosen kernel's layout for F frames
+                const int fb = A * P * (p->bits / 4);
+                const size_t need = p->tc.grid_variant == 3 ? grid_pl_smem(F, A, fb, p->jones.empty())
+                                  : p->tc.grid_variant == 2
+                                      ? grid_bal_smem(F, A, fb, p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride)
+                                      : grid_ps_smem(F, A, fb, p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
+                if (need != (size_t)p->tc.grid_smem) {
+                    p->last_error = "tensor path: gridding kernel configuration out of step (internal)";
+                    return EPIC_ERR_CUDA;
+                }
                 GridArgs g{};
                 g.volt = volt;
                 g.t0 = t0;
