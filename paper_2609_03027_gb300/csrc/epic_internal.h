@@ -60,6 +60,9 @@ struct TcState {
     int* pl_off = nullptr;         //   pairs (row-major) and where each channel's start
     int* pl_e = nullptr;           //   entries: element
     float2* pl_w = nullptr;        //   entries: weights at x and x + 1
+    int pl_max_ptr = 0;            //   most offsets / entries of one channel
+    int pl_max_ent = 0;
+    bool pl_stage = false;         //   the kernel stages a channel's lists in shared memory
     int4* gtask = nullptr;         // balanced gridding: per-channel task lists (device)
     int* gtask_off = nullptr;      // [C + 1]
     int gtask_max = 0;             // largest task list

@@ -849,15 +849,24 @@ struct GridPlArgs {
     const int* pl_off;    // [C] start of channel c's offsets in pl_ptr
     const int* pl_e;      // entries: element
     const float2* pl_w;   // entries: weights at cells x and x + 1
+    int max_ptr;          // S: most offsets of a channel (box pairs + 1)
+    int max_ent;          // S: most entries of a channel
 };
 
-__host__ __device__ inline size_t grid_pl_smem(int F, int A, int frame_bytes, bool H)
+// Shared memory of k_dftgemm_grid_pl: raw frames, unpacked voltages and, with S, one
+// channel's offsets (relative) and entries.
+__host__ __device__ inline size_t grid_pl_smem(int F, int A, int frame_bytes, bool H, bool S = false, int max_ptr = 0,
+                                              int max_ent = 0)
 {
     const size_t ap = (size_t)((frame_bytes + 15) & ~15);
-    return 2ull * F * ap + (H ? 8ull : 16ull) * F * A;
+    size_t b = 2ull * F * ap + (H ? 8ull : 16ull) * F * A;
+    if (S) b += 4ull * ((max_ptr + 1) & ~1) + 4ull * ((max_ent + 1) & ~1) + 8ull * max_ent;
+    return b;
 }
 
-template <int F, bool H>
+// S: the lists of the channel a pass grids are staged in shared memory (when they fit) instead
+// of being read through L1.
+template <int F, bool H, bool S>
 __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs pa)
 {
     const GridArgs& a = pa.g;
@@ -869,6 +878,9 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
     uint8_t* raw = gsm;                                          // [2][F][APr]
     float4* sv = reinterpret_cast<float4*>(gsm + 2 * F * APr);   // [F][A] (FP32) or [A][F] (H)
     uint2* svh = reinterpret_cast<uint2*>(sv);
+    int* sptr = reinterpret_cast<int*>(gsm + 2 * F * APr + (H ? 8 : 16) * F * A);  // S: offsets, then
+    int* sent = sptr + ((pa.max_ptr + 1) & ~1);                                    // elements and
+    float2* swt = reinterpret_cast<float2*>(sent + ((pa.max_ent + 1) & ~1));       // weights
 
     // (channel, frame) pairs [w0, w1) of this block
     const long long w0 = split_start(nullptr, a.c0, a.n_ch, 1, a.nt, blockIdx.x, gridDim.x);
@@ -898,7 +910,7 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
     };
 
     uint32_t ph = 0, pending = 0;
-    int buf = 0;
+    int buf = 0, staged = -1;
     bool ok = true;
     if (a.bulk && tid == 0) {
         fetch(w0, 0);
@@ -913,6 +925,16 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
         const int4 tp = a.tbox[c];
         const int nyh = tp.x, N1h = P * nyh;
         const uint32_t part_bytes = (uint32_t)N1h * pad64(2 * nxp) * 2;
+        if (S && cl != staged) {  // the channel's offsets (relative to its first entry) and entries
+            const int* gp = pa.pl_ptr + pa.pl_off[c];
+            const int np = nyp * (nxp >> 1) + 1, e0 = __ldg(gp), ne = __ldg(gp + np - 1) - e0;
+            for (int i = tid; i < np; i += blockDim.x) sptr[i] = __ldg(gp + i) - e0;
+            for (int i = tid; i < ne; i += blockDim.x) {
+                sent[i] = __ldg(pa.pl_e + e0 + i);
+                swt[i] = __ldg(pa.pl_w + e0 + i);
+            }
+            staged = cl;  // read by the task loop after the barrier below
+        }
         const float4* jm = a.jones ? a.jones + (size_t)c * A * 2 : nullptr;  // polarisation mixing
         if (a.bulk && tid == 0 && wn < w1) {  // the other buffer was consumed by the previous pass
             fetch(wn, buf ^ 1);
@@ -940,7 +962,9 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
         __syncthreads();
         const int half = nxp >> 1;
         const int tasks = tp.z * half;
-        const int* ptr_c = pa.pl_ptr + pa.pl_off[c];
+        const int* ptr_c = S ? sptr : pa.pl_ptr + pa.pl_off[c];
+        const int* ent_e = S ? sent : pa.pl_e;
+        const float2* ent_w = S ? swt : pa.pl_w;
         for (int task = tid; task < tasks; task += blockDim.x) {
             const int y = task / half, x = 2 * (task - y * half);
             float4 g[2][F];
@@ -948,11 +972,7 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
             for (int j = 0; j < 2; ++j)
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) g[j][fi] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int k1 = y < nyp ? __ldg(ptr_c + task + 1) : 0;
-            for (int k = y < nyp ? __ldg(ptr_c + task) : 0; k < k1; ++k) {
-                const int e = __ldg(pa.pl_e + k);
-                const float2 wv = __ldg(pa.pl_w + k);
-                float4 v[F];
+            auto load = [&](int e, float4 (&v)[F]) {  // the pass's F frames of element e
                 if constexpr (H) {
                     uint2 hv[F];
                     if constexpr (F == 1) {
@@ -976,6 +996,8 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
 #pragma unroll
                     for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + e];
                 }
+            };
+            auto apply = [&](float2 wv, const float4 (&v)[F]) {
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) {
                     g[0][fi].x = fmaf(wv.x, v[fi].x, g[0][fi].x);
@@ -987,6 +1009,22 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
                     g[1][fi].z = fmaf(wv.y, v[fi].z, g[1][fi].z);
                     g[1][fi].w = fmaf(wv.y, v[fi].w, g[1][fi].w);
                 }
+            };
+            const int k1 = y < nyp ? ptr_c[task + 1] : 0;
+            int k = y < nyp ? ptr_c[task] : 0;
+            for (; k + 1 < k1; k += 2) {  // two list entries in flight, applied in list order
+                const int e0 = ent_e[k], e1 = ent_e[k + 1];
+                const float2 w0 = ent_w[k], w1 = ent_w[k + 1];
+                float4 v0[F], v1[F];
+                load(e0, v0);
+                load(e1, v1);
+                apply(w0, v0);
+                apply(w1, v1);
+            }
+            if (k < k1) {
+                float4 v0[F];
+                load(ent_e[k], v0);
+                apply(ent_w[k], v0);
             }
             const int kc_re = x >> 3, kc_im = (nxp + x) >> 3, within = (x & 7) * 2;
             const int hpart = y / nyh, R0 = y - hpart * nyh;
@@ -2653,12 +2691,17 @@ static epic_status grid_pl_config(epic_plan_s* p, int F)
 {
     if (!p->tc.pl_ptr || (F != 1 && F != 2 && F != 4 && F != 8)) return EPIC_ERR_UNSUPPORTED;
     const bool H = p->jones.empty();  // FP16-pair voltages unless polarisation mixing
-    const size_t bytes = grid_pl_smem(F, p->A, p->A * p->P * (p->bits / 4), H);
-    const void* fn = nullptr;
-    if (H) fn = F == 8 ? (const void*)k_dftgemm_grid_pl<8, true> : F == 4 ? (const void*)k_dftgemm_grid_pl<4, true>
-              : F == 2 ? (const void*)k_dftgemm_grid_pl<2, true> : (const void*)k_dftgemm_grid_pl<1, true>;
-    else fn = F == 8 ? (const void*)k_dftgemm_grid_pl<8, false> : F == 4 ? (const void*)k_dftgemm_grid_pl<4, false>
-              : F == 2 ? (const void*)k_dftgemm_grid_pl<2, false> : (const void*)k_dftgemm_grid_pl<1, false>;
+    const int fb = p->A * p->P * (p->bits / 4);
+    // the lists in shared memory when they fit beside the voltages
+    const bool S =
+        grid_pl_smem(F, p->A, fb, H, true, p->tc.pl_max_ptr, p->tc.pl_max_ent) + 2048 <= (size_t)p->smem_optin;
+    const size_t bytes = grid_pl_smem(F, p->A, fb, H, S, p->tc.pl_max_ptr, p->tc.pl_max_ent);
+#define EPIC_PL_FN(FF)                                                                                   \
+    (H ? (S ? (const void*)k_dftgemm_grid_pl<FF, true, true> : (const void*)k_dftgemm_grid_pl<FF, true, false>) \
+       : (S ? (const void*)k_dftgemm_grid_pl<FF, false, true> : (const void*)k_dftgemm_grid_pl<FF, false, false>))
+    const void* fn = F == 8 ? EPIC_PL_FN(8) : F == 4 ? EPIC_PL_FN(4) : F == 2 ? EPIC_PL_FN(2) : EPIC_PL_FN(1);
+#undef EPIC_PL_FN
+    p->tc.pl_stage = S;
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncGetAttributes(k_dftgemm_grid_pl)");
@@ -3188,6 +3231,11 @@ epic_status dftgemm_setup(epic_plan_s* p)
         }
         toff[C] = (int)tasks.size();
         eoff[C] = (int)ell_e.size();
+        for (int c = 0; c < C; ++c) {  // largest offsets / entries of a channel (staged lists)
+            const int np = p->box[c].ny * (p->box[c].nx / kTaskCells) + 1;
+            p->tc.pl_max_ptr = std::max(p->tc.pl_max_ptr, np);
+            p->tc.pl_max_ent = std::max(p->tc.pl_max_ent, pl_ptr[pl_off[c] + np - 1] - pl_ptr[pl_off[c]]);
+        }
         if (kTaskCells == 2 && !pl_e.empty() && pl_e.size() < (1u << 31)) {  // pair lists for k_dftgemm_grid_pl
             e = cudaMalloc(&p->tc.pl_ptr, pl_ptr.size() * sizeof(int));
             if (e == cudaSuccess)
@@ -3369,7 +3417,8 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             if (p->tc.grid_ps || p->tc.grid_variant >= 2) {
                 // the launch's shared memory must be the chosen kernel's layout for F frames
                 const int fb = A * P * (p->bits / 4);
-                const size_t need = p->tc.grid_variant == 3 ? grid_pl_smem(F, A, fb, p->jones.empty())
+                const size_t need = p->tc.grid_variant == 3 ? grid_pl_smem(F, A, fb, p->jones.empty(), p->tc.pl_stage,
+                                                                             p->tc.pl_max_ptr, p->tc.pl_max_ent)
                                   : p->tc.grid_variant == 2
                                       ? grid_bal_smem(F, A, fb, p->tc.gtask_max, p->tc.gell_max, (unsigned)p->tc.stride)
                                       : grid_ps_smem(F, A, fb, p->tc.grid_max_cells, p->tc.grid_max_list, p->tc.grid_cplx);
@@ -3409,18 +3458,22 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     pa.pl_off = p->tc.pl_off;
                     pa.pl_e = p->tc.pl_e;
                     pa.pl_w = reinterpret_cast<const float2*>(p->tc.pl_w);
+                    pa.max_ptr = p->tc.pl_max_ptr;
+                    pa.max_ent = p->tc.pl_max_ent;
                     const size_t sm = p->tc.grid_smem;
+#define EPIC_PL_LAUNCH(FF, HH, SS) k_dftgemm_grid_pl<FF, HH, SS><<<gb, kGridPlThreads, sm, s>>>(pa)
+#define EPIC_PL_F(HH, SS)                       \
+    if (F == 8) EPIC_PL_LAUNCH(8, HH, SS);      \
+    else if (F == 4) EPIC_PL_LAUNCH(4, HH, SS); \
+    else if (F == 2) EPIC_PL_LAUNCH(2, HH, SS); \
+    else EPIC_PL_LAUNCH(1, HH, SS);
                     if (p->jones.empty()) {
-                        if (F == 8) k_dftgemm_grid_pl<8, true><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else if (F == 4) k_dftgemm_grid_pl<4, true><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else if (F == 2) k_dftgemm_grid_pl<2, true><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else k_dftgemm_grid_pl<1, true><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        if (p->tc.pl_stage) { EPIC_PL_F(true, true) } else { EPIC_PL_F(true, false) }
                     } else {
-                        if (F == 8) k_dftgemm_grid_pl<8, false><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else if (F == 4) k_dftgemm_grid_pl<4, false><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else if (F == 2) k_dftgemm_grid_pl<2, false><<<gb, kGridPlThreads, sm, s>>>(pa);
-                        else k_dftgemm_grid_pl<1, false><<<gb, kGridPlThreads, sm, s>>>(pa);
+                        if (p->tc.pl_stage) { EPIC_PL_F(false, true) } else { EPIC_PL_F(false, false) }
                     }
+#undef EPIC_PL_F
+#undef EPIC_PL_LAUNCH
                 } else if (p->tc.grid_variant == 2) {
                     GridBalArgs ba{};
                     ba.g = g;
