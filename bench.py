@@ -385,7 +385,7 @@ def main():
     ap.add_argument("--impl", default="epic", choices=["epic", "reference"])
     ap.add_argument("--path", default="dftgemm", choices=["plain", "fused", "dftgemm", "auto"])
     ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3, 4, 6])
-    ap.add_argument("--compare", default="plain", help="also time this path (comma list, '' for none)")
+    ap.add_argument("--compare", default="plain", help="also time this path (comma list; 'none' or '' for none)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-time", type=int, default=250, help="time samples per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -504,7 +504,7 @@ def main():
 
     # the plain comparator (and any other path) on the same inputs
     compare = {}
-    for cp in [c for c in args.compare.split(",") if c and c != args.path]:
+    for cp in [c for c in args.compare.split(",") if c and c not in (args.path, "none")]:
         cms, ck, _, _, _ = time_path(cp, max(3, args.steps // 4), 3)
         cms = reduce_max(cms, world, dev)
         compare[cp] = {"value": units * world / (cms / 1e3), "ms_per_step": cms}
