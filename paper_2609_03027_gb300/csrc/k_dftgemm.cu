@@ -2275,7 +2275,9 @@ __device__ __noinline__ void ws3_split_finish(const MmaArgs& a, int item, int c,
     }
 }
 
-template <int MODE>  // 0: whole items, 1: equal shares (split items), 2: whole items, sub-integrations
+// MODE 0: whole items, 1: equal shares (split items), 2: whole items, sub-integrations.
+// PARTS: some channel of the plan has more than one row part (else every H is 1 at compile time).
+template <int MODE, bool PARTS>
 __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -2354,7 +2356,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const int c = a.c0 + cl;
             const int4 bx = a.box[c];
             const int4 tp = a.tbox[c];
-            const int nxp = bx.z, nyh = tp.x, H = tp.y;
+            const int nxp = bx.z, nyh = tp.x, H = PARTS ? tp.y : 1;
             const int K1 = 2 * nxp, K2h = 2 * nyh, N1 = P * nyh;
             const int NU = nt * H;  // sub-frames u = t H + h: frame t, row part h
             const uint32_t part_bytes = (uint32_t)N1 * pad64(K1) * 2;
@@ -2494,7 +2496,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const int g = item % a.n_g, kb = (item / a.n_g) % a.n_kb, cl = item / (a.n_g * a.n_kb);
             const int c = a.c0 + cl;
             const int4 tp = a.tbox[c];
-            const int nyh = tp.x, H = tp.y, nyt = tp.z;
+            const int nyh = tp.x, H = PARTS ? tp.y : 1, nyt = tp.z;
             if (warp < 4) {  // stage-2 DFT operand (every row part) -> TMEM (lane = ky row)
                 const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * nyt;
                 for (int jj = 0; jj < nyt; jj += 8) {
@@ -3345,9 +3347,12 @@ epic_status dftgemm_setup(epic_plan_s* p)
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute(k_dftgemm_grid)");
     e = allow_max_smem((const void*)k_dftgemm_ws<0>, p->smem_optin);
     if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws2<0>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1>, p->smem_optin);
-    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0, false>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1, false>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2, false>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<0, true>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<1, true>, p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_smem((const void*)k_dftgemm_ws3<2, true>, p->smem_optin);
     p->tc.ws_variant = p->tc.ws ? 3 : 0;
     if (p->tc.ws && p->sm_count > kWs3MaxBlocks) p->tc.ws_variant = 1;
     if (p->tc.parts && p->tc.ws_variant != 3) {
@@ -3549,11 +3554,14 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     a.partial = p->tc.partial;
                     a.counters = p->tc.counters;
                     if (p->sub > 0)
-                        k_dftgemm_ws3<2><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                        p->tc.parts ? k_dftgemm_ws3<2, true><<<grid, kWs3Threads, p->tc.smem, s>>>(a)
+                                    : k_dftgemm_ws3<2, false><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
                     else if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
-                        k_dftgemm_ws3<1><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a);
+                        p->tc.parts ? k_dftgemm_ws3<1, true><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a)
+                                    : k_dftgemm_ws3<1, false><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a);
                     else
-                        k_dftgemm_ws3<0><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
+                        p->tc.parts ? k_dftgemm_ws3<0, true><<<grid, kWs3Threads, p->tc.smem, s>>>(a)
+                                    : k_dftgemm_ws3<0, false><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
                 }
                 else if (p->tc.ws_variant == 2) k_dftgemm_ws2<0><<<grid, kWs2Threads, p->tc.smem, s>>>(a);
                 else k_dftgemm_ws<0><<<grid, kWsThreads, p->tc.smem, s>>>(a);
