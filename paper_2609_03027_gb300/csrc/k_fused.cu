@@ -8,7 +8,7 @@
 //   into shared memory, then transform the rows only at the slab's SW columns, as
 //   direct sums over the box's occupied columns (the other columns of a row are
 //   zero; a full row FFT would compute N - SW outputs this item does not use);
-//   FFT the slab's columns of both pols as one batch (radix-2 Stockham, + sign;
+//   FFT the slab's columns of both pols as one batch (radix-4/2 Stockham, + sign;
 //   only the occupied rows are non-zero);
 //   XX, YY, Re/Im XY of the slab's SW x N pixels are added to registers.
 // The fftshift is folded into the gridding weights, so transform index k is image
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kFMaxThreads, 1) k_fused_fp32(FusedArgs a)
                 const int yr = y - y0;
                 fa[pk * ldc + y] = (yr >= 0 && yr < nyp) ? hbuf[(p * a.box_y + yr) * hs + k] : make_float2(0.f, 0.f);
             }
-            const float2* res = fft_stockham_r2(fa, fb, a.logN, P * SW, 1, ldc, tw);
+            const float2* res = fft_stockham(fa, fb, a.logN, P * SW, 1, ldc, tw);
             // ---- products of this thread's pixels (kx = kxl, ky = ky0 + j kys)
 #pragma unroll
             for (int j = 0; j < NPT; ++j) {

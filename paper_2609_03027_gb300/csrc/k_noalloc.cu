@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_fft_rows(float2* __restrict__
     const size_t r0 = (size_t)blockIdx.x * rows_per_cta;
     const int nr = (int)min((size_t)rows_per_cta, n_rows - r0);
     for (int i = threadIdx.x; i < nr * N; i += blockDim.x) a[i] = grid[r0 * N + i];
-    float2* res = epic::fft_stockham_r2(a, b, logN, nr, 1, N, tw);
+    float2* res = epic::fft_stockham(a, b, logN, nr, 1, N, tw);
     for (int i = threadIdx.x; i < nr * N; i += blockDim.x) grid[r0 * N + i] = res[i];
 }
 
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_fft_cols(float2* __restrict__
         const int row = i / tile, col = i - row * tile;
         a[col * ld + row] = g[(size_t)row * N + x0 + col];
     }
-    float2* res = epic::fft_stockham_r2(a, b, logN, tile, 1, ld, tw);
+    float2* res = epic::fft_stockham(a, b, logN, tile, 1, ld, tw);
     for (int i = threadIdx.x; i < N * tile; i += blockDim.x) {
         const int row = i / tile, col = i - row * tile;
         g[(size_t)row * N + x0 + col] = res[col * ld + row];

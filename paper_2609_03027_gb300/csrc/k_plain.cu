@@ -4,7 +4,7 @@
 //   k_plain_grid     unpack the voltages (and mix polarisations, when the plan
 //                    has a mixing kernel) and gather-grid every (t, c, p)
 //                    frame onto a full N x N complex grid (Eq. 1 bracket)
-//   k_plain_fft_rows radix-2 Stockham FFT along x of every grid row (Eq. 1 sum)
+//   k_plain_fft_rows radix-4/2 Stockham FFT along x of every grid row (Eq. 1 sum)
 //   k_plain_fft_cols the same along y, on 16-column tiles
 //   k_plain_sqacc    XX, YY, XY products summed over the chunk's frames and
 //                    added to the images (Eq. 2)
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_plain_fft_rows(float2* __restrict_
     const float2* src = grid + r0 * N;
     for (int i = threadIdx.x; i < nr * N; i += blockDim.x) a[i] = src[i];
     __syncthreads();
-    float2* res = fft_stockham_r2(a, b, logN, nr, 1, N, tw);
+    float2* res = fft_stockham(a, b, logN, nr, 1, N, tw);
     float2* dst = grid + r0 * N;
     for (int i = threadIdx.x; i < nr * N; i += blockDim.x) dst[i] = res[i];
 }
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_plain_fft_cols(float2* __restrict_
         a[col * ld + row] = g[(size_t)row * N + x0 + col];
     }
     __syncthreads();
-    float2* res = fft_stockham_r2(a, b, logN, tile, 1, ld, tw);
+    float2* res = fft_stockham(a, b, logN, tile, 1, ld, tw);
     for (int i = threadIdx.x; i < N * tile; i += blockDim.x) {
         const int row = i / tile, col = i - row * tile;
         g[(size_t)row * N + x0 + col] = res[col * ld + row];

@@ -83,27 +83,62 @@ __device__ __forceinline__ void stage_frame(float2* dst, const uint8_t* frame, i
     }
 }
 
-// Radix-2 Stockham autosort FFT with the + sign (Eq. 1), unnormalised, on
-// `batch` transforms of length n = 2^logn held in shared memory: element i of
-// transform q is buf[q * bs + i * es].  Ping-pongs between a and b; returns the
-// buffer holding the natural-order result.  tw[m] = exp(+2 pi i m / n), m < n/2.
+// Stockham autosort FFT with the + sign (Eq. 1), unnormalised, on `batch` transforms of
+// length n = 2^logn held in shared memory: element i of transform q is buf[q * bs + i * es].
+// Radix-4 stages (spans 1, 4, 16, ...), then one radix-2 stage when logn is odd, so a
+// transform takes ceil(logn / 2) passes over shared memory (N = 128: 4 instead of 7).  A
+// radix-4 stage of span L turns v_r = a[j + r n/4] w^(r k n / 4L) (k = j mod L, w =
+// exp(+2 pi i / n)) into the 4-point DFT y_q = sum_r v_r i^(r q), stored at
+// (j / L) 4L + k + q L.  Ping-pongs between a and b; returns the buffer holding the
+// natural-order result.  tw[m] = exp(+2 pi i m / n), m < n/2 (w^m = -tw[m - n/2] above).
 // Ends with __syncthreads(); all threads of the block must call it.
-__device__ __forceinline__ float2* fft_stockham_r2(float2* a, float2* b, int logn, int batch, int es, int bs,
-                                                   const float2* tw)
+__device__ __forceinline__ float2* fft_stockham(float2* a, float2* b, int logn, int batch, int es, int bs,
+                                                const float2* tw)
 {
-    const int half = 1 << (logn - 1);
+    const int n = 1 << logn, n4 = n >> 2, half = n >> 1;
+    auto W = [&](int m) {
+        const float2 t = tw[m < half ? m : m - half];
+        return m < half ? t : make_float2(-t.x, -t.y);
+    };
     __syncthreads();
-    for (int s = 0; s < logn; ++s) {
-        const int Ns = 1 << s;
+    int ls = 0;
+    for (; ls + 2 <= logn; ls += 2) {
+        const int L = 1 << ls;
+        for (int w = threadIdx.x; w < batch * n4; w += blockDim.x) {
+            const int q = w >> (logn - 2);
+            const int j = w & (n4 - 1);
+            const int k = j & (L - 1);
+            const int e1 = k << (logn - 2 - ls);
+            const float2* src = a + q * bs;
+            const float2 v0 = src[j * es];
+            const float2 v1 = cmul(src[(j + n4) * es], W(e1));
+            const float2 v2 = cmul(src[(j + 2 * n4) * es], W(2 * e1));
+            const float2 v3 = cmul(src[(j + 3 * n4) * es], W(3 * e1));
+            const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+            const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+            const int idx = ((j >> ls) << (ls + 2)) + k;
+            float2* dst = b + q * bs;
+            dst[idx * es] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            dst[(idx + L) * es] = make_float2(d02.x - d13.y, d02.y + d13.x);      // + i (v1 - v3)
+            dst[(idx + 2 * L) * es] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            dst[(idx + 3 * L) * es] = make_float2(d02.x + d13.y, d02.y - d13.x);  // - i (v1 - v3)
+        }
+        __syncthreads();
+        float2* t = a;
+        a = b;
+        b = t;
+    }
+    if (ls < logn) {  // the last factor 2
+        const int L = 1 << ls;
         for (int w = threadIdx.x; w < batch * half; w += blockDim.x) {
             const int q = w >> (logn - 1);
             const int j = w & (half - 1);
-            const int k = j & (Ns - 1);
+            const int k = j & (L - 1);
             const float2 v0 = a[q * bs + j * es];
-            const float2 v1 = cmul(a[q * bs + (j + half) * es], tw[k << (logn - 1 - s)]);
-            const int idx = ((j >> s) << (s + 1)) + k;
+            const float2 v1 = cmul(a[q * bs + (j + half) * es], tw[k << (logn - 1 - ls)]);
+            const int idx = ((j >> ls) << (ls + 1)) + k;
             b[q * bs + idx * es] = make_float2(v0.x + v1.x, v0.y + v1.y);
-            b[q * bs + (idx + Ns) * es] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            b[q * bs + (idx + L) * es] = make_float2(v0.x - v1.x, v0.y - v1.y);
         }
         __syncthreads();
         float2* t = a;
