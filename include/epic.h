@@ -218,7 +218,9 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  * the plan configured with them.  Parameters by path:
  *   AUTO plans    path         0 plain FP32, 1 fused FP32, 2 DFT-as-GEMM (timed first; the chosen
  *                              path's own parameters follow)
- *   PLAIN_FP32    chunk_mb     grid-buffer budget of one time chunk (MiB)
+ *   PLAIN_FP32    fft          FFT kernels: 0 register-resident two-pass transforms (one
+ *                              shared-memory exchange), 1 radix-4/2 Stockham in shared memory
+ *                 chunk_mb     grid-buffer budget of one time chunk (MiB)
  *   FUSED_FP32    slab         image columns per work item
  *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
  *                              control warp does, 3: a control warpgroup with its own

@@ -149,6 +149,7 @@ struct epic_plan_s {
     int fused_variant = 0;                // kernel variant chosen for fused paths
     bool auto_path = false;               // created with EPIC_PATH_AUTO: the tuner may change path
     int slab = 0;                         // output columns per work item (fused paths)
+    int plain_fft = 0;                    // plain path FFT kernels: 0 register two-pass, 1 shared-memory Stockham
 
     size_t chunk_budget = 0;              // scratch budget of one time chunk (chunked paths)
 
@@ -204,6 +205,7 @@ epic_status image_run_with(epic_plan_s* p, CallScratch& c, const uint8_t* volt, 
 epic_status plain_setup(epic_plan_s* p);
 epic_status plain_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
 epic_status plain_set_chunk(epic_plan_s* p, size_t budget);
+epic_status plain_set_fft(epic_plan_s* p, int v);
 
 // k_fused.cu
 epic_status fused_setup(epic_plan_s* p);

@@ -17,6 +17,7 @@ struct Knob {
 };
 
 epic_status set_plain_chunk(epic_plan_s* p, int mb) { return epic::plain_set_chunk(p, (size_t)mb << 20); }
+epic_status set_plain_fft(epic_plan_s* p, int v) { return epic::plain_set_fft(p, v); }
 epic_status set_dft_chunk(epic_plan_s* p, int mb) { return epic::dftgemm_set_chunk(p, (size_t)mb << 20); }
 epic_status set_dft_frames(epic_plan_s* p, int f) { return epic::dftgemm_grid_config(p, f); }
 epic_status set_fused_slab(epic_plan_s* p, int sw) { return epic::fused_set_slab(p, sw); }
@@ -34,6 +35,7 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
         knobs.push_back({"path", {EPIC_PATH_PLAIN_FP32, EPIC_PATH_FUSED_FP32, EPIC_PATH_DFTGEMM_FP16}, p->path,
                          set_path});
     if (p->path == EPIC_PATH_PLAIN_FP32) {
+        knobs.push_back({"fft", {0, 1}, p->plain_fft, set_plain_fft});
         knobs.push_back({"chunk_mb", {128, 256, 512, 1024}, budget_mb, set_plain_chunk});
     } else if (p->path == EPIC_PATH_FUSED_FP32) {
         knobs.push_back({"slab", {8, 16, 32}, p->slab, set_fused_slab});

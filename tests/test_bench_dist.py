@@ -49,19 +49,19 @@ def test_recorded_traffic_only_for_the_captured_launch_configuration():
     sys.path.insert(0, ROOT)
     import bench
     import epic_synth as synth
-    cfg = synth.config(2)
-    rec = bench.json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_dftgemm_ws3@cfg2"]
-    got = bench.recorded_traffic("k_dftgemm_ws3", 2, 250, cfg, dict(rec["params"]))
+    cfg = synth.config(3)
+    rec = bench.json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_dftgemm_ws3@cfg3"]
+    got = bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, dict(rec["params"]))
     src = open(os.path.join(ROOT, "paper_2609_03027_gb300", "csrc", rec["source"]), "rb").read()
     if bench.hashlib.sha256(src).hexdigest()[:16] != rec["sha"]:
         assert got is None                         # kernel changed since the capture
         return
     assert got == pytest.approx(rec["bytes_per_sample"] * 250)
     other = dict(rec["params"], chunk_mb=192)
-    assert bench.recorded_traffic("k_dftgemm_ws3", 2, 250, cfg, other) is None
-    assert bench.recorded_traffic("k_dftgemm_ws3", 2, 250, cfg, None) is None
+    assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, other) is None
+    assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, None) is None
     import dataclasses
-    assert bench.recorded_traffic("k_dftgemm_ws3", 2, 250, dataclasses.replace(cfg, input_bits=8),
+    assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, dataclasses.replace(cfg, input_bits=8),
                                   dict(rec["params"])) is None
 
 
