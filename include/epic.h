@@ -222,15 +222,19 @@ epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
  *                              shared-memory exchange), 1 radix-4/2 Stockham in shared memory
  *                 chunk_mb     grid-buffer budget of one time chunk (MiB)
  *   FUSED_FP32    slab         image columns per work item
- *   DFTGEMM_FP16  mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
+ *   DFTGEMM_FP16  group        channels per launch: 0 groups of about two work items per SM,
+ *                              1 every channel in one launch (fewer launches, larger tile buffer)
+ *                 mma_kernel   1: epilogue warps issue the tensor-core work, 2: a
  *                              control warp does, 3: a control warpgroup with its own
  *                              register budget does (when the occupied box allows each);
- *                 split        work of the control-warp kernel: -1 automatic, 0 whole work
- *                              items per SM, 1 equal (item, time sample) shares per SM;
+ *                 split        work of the control-warp kernel: -1 automatic (equal shares unless
+ *                              the items divide evenly), 0 whole work items per SM, 1 equal
+ *                              (item, time sample) shares per SM;
  *                 grid_kernel  gridding kernel: 1 row-major cell walk, 2 cells in lists sorted
  *                              by length (Gaussian GCF, when its tiles fit in shared memory);
  *                 grid_frames  frames per pass of the gridding kernel;
- *                 chunk_mb     tile-buffer budget of one (channel group, time chunk)
+ *                 chunk_mb     tile-buffer budget of one (channel group, time chunk), 96 MiB to
+ *                              24 GiB (the block's samples at most)
  * Images after tuning equal those before up to FP32 rounding order.  reps calls
  * are timed per candidate (1..100) after one untimed call.  May reallocate the
  * plan's scratch (EPIC_ERR_OOM if that fails; the plan then keeps working with

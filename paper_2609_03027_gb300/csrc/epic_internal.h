@@ -83,6 +83,8 @@ struct TcState {
     float* partial = nullptr;      // k_dftgemm_ws3: partial sums of items split between blocks
     int* counters = nullptr;       // k_dftgemm_ws3: per item, parts stored so far
     int split = -1;                // k_dftgemm_ws3 work split: -1 auto, 0 whole items, 1 equal shares
+    int group = 0;                 // channels per launch: 0 groups of about two work items per SM,
+    int cg_items = 0;              //   1 every channel (cg_items: the size group 0 gives)
     // Row parts of k_dftgemm_ws3: channel c's box rows are cut into H parts of nyh rows
     // (padded to H * nyh rows, the extra rows zero); each part is a grid tile of its own
     // (P * nyh rows) and a stage-1 / stage-2 step of its own, so tall boxes fit in TMEM.
@@ -220,5 +222,6 @@ epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant);
 epic_status dftgemm_set_grid_kernel(epic_plan_s* p, int variant);
 epic_status dftgemm_set_split(epic_plan_s* p, int mode);
+epic_status dftgemm_set_group(epic_plan_s* p, int v);
 
 }  // namespace epic

@@ -997,17 +997,17 @@ __global__ void __launch_bounds__(kGridPlThreads) k_dftgemm_grid_pl(GridPlArgs p
                     for (int fi = 0; fi < F; ++fi) v[fi] = sv[fi * A + e];
                 }
             };
-            auto apply = [&](float2 wv, const float4 (&v)[F]) {
+            auto apply = [&](float2 wv, const float4 (&v)[F]) {  // packed FP32 FMAs, rounded as fmaf
+                const float2 w0 = make_float2(wv.x, wv.x), w1 = make_float2(wv.y, wv.y);
 #pragma unroll
                 for (int fi = 0; fi < F; ++fi) {
-                    g[0][fi].x = fmaf(wv.x, v[fi].x, g[0][fi].x);
-                    g[0][fi].y = fmaf(wv.x, v[fi].y, g[0][fi].y);
-                    g[0][fi].z = fmaf(wv.x, v[fi].z, g[0][fi].z);
-                    g[0][fi].w = fmaf(wv.x, v[fi].w, g[0][fi].w);
-                    g[1][fi].x = fmaf(wv.y, v[fi].x, g[1][fi].x);
-                    g[1][fi].y = fmaf(wv.y, v[fi].y, g[1][fi].y);
-                    g[1][fi].z = fmaf(wv.y, v[fi].z, g[1][fi].z);
-                    g[1][fi].w = fmaf(wv.y, v[fi].w, g[1][fi].w);
+                    const float2 vx = make_float2(v[fi].x, v[fi].y), vy = make_float2(v[fi].z, v[fi].w);
+                    const float2 a0 = tc::fma2(w0, vx, make_float2(g[0][fi].x, g[0][fi].y));
+                    const float2 b0 = tc::fma2(w0, vy, make_float2(g[0][fi].z, g[0][fi].w));
+                    const float2 a1 = tc::fma2(w1, vx, make_float2(g[1][fi].x, g[1][fi].y));
+                    const float2 b1 = tc::fma2(w1, vy, make_float2(g[1][fi].z, g[1][fi].w));
+                    g[0][fi] = make_float4(a0.x, a0.y, b0.x, b0.y);
+                    g[1][fi] = make_float4(a1.x, a1.y, b1.x, b1.y);
                 }
             };
             const int k1 = y < nyp ? ptr_c[task + 1] : 0;
@@ -1645,11 +1645,9 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r)
 // family): each lane rounds exactly as fmaf does, in half the issue slots.
 __device__ __forceinline__ void fma2x2(float& c0, float& c1, float a0, float a1, float b0, float b1)
 {
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%0, %1};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
-        : "+f"(c0), "+f"(c1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    const float2 r = tc::fma2(make_float2(a0, a1), make_float2(b0, b1), make_float2(c0, c1));
+    c0 = r.x;
+    c1 = r.y;
 }
 
 // Products of W pixels (TMEM loads of X re / im and Y re / im, W even) added to the
@@ -2498,12 +2496,22 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             const int4 tp = a.tbox[c];
             const int nyh = tp.x, H = PARTS ? tp.y : 1, nyt = tp.z;
             if (warp < 4) {  // stage-2 DFT operand (every row part) -> TMEM (lane = ky row)
-                const uint32_t* src = a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] + (size_t)(32 * warp + lane) * nyt;
-                for (int jj = 0; jj < nyt; jj += 8) {
-                    uint32_t r[8];
+                // rows of nyt words (a multiple of 8) from a 32-byte aligned table: 32 words per
+                // round of 16-byte loads, so an item waits for nyt / 32 load latencies, not nyt / 8
+                const uint4* src = reinterpret_cast<const uint4*>(a.a2w + a.a2w_off[(size_t)c * a.n_kb + kb] +
+                                                                  (size_t)(32 * warp + lane) * nyt);
+                for (int jj = 0; jj < nyt; jj += 32) {
+                    uint4 q[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) r[i] = src[jj + i];
-                    tc::tmem_st8(tmem + lane_base + a2col + jj, r);
+                    for (int i = 0; i < 8; ++i)
+                        q[i] = jj + 4 * i < nyt ? __ldg(src + (jj >> 2) + i) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if (jj + 8 * g >= nyt) break;
+                        const uint32_t r[8] = {q[2 * g].x,     q[2 * g].y,     q[2 * g].z,     q[2 * g].w,
+                                               q[2 * g + 1].x, q[2 * g + 1].y, q[2 * g + 1].z, q[2 * g + 1].w};
+                        tc::tmem_st8(tmem + lane_base + a2col + jj + 8 * g, r);
+                    }
                 }
                 tc::tmem_wait_st();
             }
@@ -2653,8 +2661,27 @@ epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
     return EPIC_OK;
 }
 
-// Work split of k_dftgemm_ws3: -1 = automatic (equal shares when a launch has fewer
-// items than SMs), 0 = whole items per block, 1 = equal (item, frame) shares.
+// Channels per launch of the warp-specialised kernels: 0 = groups of about two work items
+// per SM (whole items per block balance), 1 = every channel in one group (the fewest
+// launches; with equal (item, frame) shares the item count need not divide evenly).  The
+// tile buffer is resized for the group at the current chunk budget.
+epic_status dftgemm_set_group(epic_plan_s* p, int v)
+{
+    if (!p->tc.ws || v < 0 || v > 1) return EPIC_ERR_UNSUPPORTED;
+    const int cg_old = p->tc.cg, group_old = p->tc.group;
+    p->tc.group = v;
+    p->tc.cg = v == 1 ? p->C : p->tc.cg_items;
+    epic_status st = dftgemm_set_chunk(p, p->chunk_budget);
+    if (st != EPIC_OK) {
+        p->tc.group = group_old;
+        p->tc.cg = cg_old;
+        dftgemm_set_chunk(p, p->chunk_budget);
+    }
+    return st;
+}
+
+// Work split of k_dftgemm_ws3: -1 = automatic (equal shares unless the launch's items are
+// a whole number per SM), 0 = whole items per block, 1 = equal (item, frame) shares.
 epic_status dftgemm_set_split(epic_plan_s* p, int mode)
 {
     if (!p->tc.ws || mode < -1 || mode > 1 || (p->sub > 0 && mode == 1)) return EPIC_ERR_UNSUPPORTED;
@@ -3084,7 +3111,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
         stride = std::max(stride, (size_t)P * p->tc.tbox_h[c].z * pad64(2 * p->box[c].nx) * 2);
     stride = align_up(stride, 128);
     const int per_ch = n_kb * (p->tc.ws ? n_gp : n_s);
-    p->tc.cg = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
+    p->tc.cg_items = std::min(C, std::max(1, (2 * p->sm_count + per_ch - 1) / per_ch));
+    p->tc.cg = p->tc.group == 1 && p->tc.ws ? C : p->tc.cg_items;
     p->tc.stride = stride;
     epic_status cst = dftgemm_set_chunk(p, kScratchBudget);
     if (cst != EPIC_OK) return cst;
@@ -3364,7 +3392,7 @@ epic_status dftgemm_setup(epic_plan_s* p)
         return EPIC_ERR_UNSUPPORTED;
     }
     if (p->tc.ws && e == cudaSuccess) {
-        const size_t n_items = (size_t)p->tc.cg * n_kb * n_gp;
+        const size_t n_items = (size_t)C * n_kb * n_gp;  // the largest channel group
         e = cudaMalloc(&p->tc.partial, (size_t)p->sm_count * 2 * 4 * 8192 * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&p->tc.counters, n_items * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->tc.counters, 0, n_items * sizeof(int));
@@ -3556,7 +3584,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
                     if (p->sub > 0)
                         p->tc.parts ? k_dftgemm_ws3<2, true><<<grid, kWs3Threads, p->tc.smem, s>>>(a)
                                     : k_dftgemm_ws3<2, false><<<grid, kWs3Threads, p->tc.smem, s>>>(a);
-                    else if (p->tc.split == 1 || (p->tc.split < 0 && items < p->sm_count))
+                    else if (p->tc.split == 1 || (p->tc.split < 0 && items % p->sm_count != 0))
                         p->tc.parts ? k_dftgemm_ws3<1, true><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a)
                                     : k_dftgemm_ws3<1, false><<<p->sm_count, kWs3Threads, p->tc.smem, s>>>(a);
                     else

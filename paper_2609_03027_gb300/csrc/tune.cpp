@@ -24,6 +24,7 @@ epic_status set_fused_slab(epic_plan_s* p, int sw) { return epic::fused_set_slab
 epic_status set_dft_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_kernel(p, v); }
 epic_status set_dft_grid_kernel(epic_plan_s* p, int v) { return epic::dftgemm_set_grid_kernel(p, v); }
 epic_status set_dft_split(epic_plan_s* p, int v) { return epic::dftgemm_set_split(p, v); }
+epic_status set_dft_group(epic_plan_s* p, int v) { return epic::dftgemm_set_group(p, v); }
 epic_status set_path(epic_plan_s* p, int v) { return epic::set_path(p, v); }
 
 // the tuning parameters of a plan's path with their candidate and current values
@@ -40,6 +41,7 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
     } else if (p->path == EPIC_PATH_FUSED_FP32) {
         knobs.push_back({"slab", {8, 16, 32}, p->slab, set_fused_slab});
     } else if (p->path == EPIC_PATH_DFTGEMM_FP16) {
+        if (p->tc.ws) knobs.push_back({"group", {0, 1}, p->tc.group, set_dft_group});
         if (p->tc.ws && p->sub == 0) {  // sub-integrations use the control-warp kernel on whole items
             knobs.push_back({"mma_kernel", {1, 2, 3}, p->tc.ws_variant, set_dft_kernel});
             knobs.push_back({"split", {-1, 0, 1}, p->tc.split, set_dft_split});
@@ -48,7 +50,7 @@ std::vector<Knob> knobs_for(const epic_plan_s* p)
             knobs.push_back({"grid_kernel", {1, 2, 3}, p->tc.grid_variant, set_dft_grid_kernel});
         if (p->tc.grid_ps || p->tc.gtask || p->tc.pl_ptr)
             knobs.push_back({"grid_frames", {1, 2, 4, 8}, p->tc.grid_frames, set_dft_frames});
-        knobs.push_back({"chunk_mb", {96, 192, 384, 768, 1536, 3072}, budget_mb, set_dft_chunk});
+        knobs.push_back({"chunk_mb", {96, 192, 384, 768, 1536, 3072, 6144, 12288, 24576}, budget_mb, set_dft_chunk});
     }
     return knobs;
 }
