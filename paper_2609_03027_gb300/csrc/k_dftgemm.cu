@@ -2280,7 +2280,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar_a, d1_full[2], b2_full[2], b2_free[2], d2_full, d2_empty, tile_full[kWs3MaxTileBufs],
-        drain[2];
+        tile_free[kWs3MaxTileBufs], drain[2];
     __shared__ uint32_t tmem_sh;
     __shared__ int err_sh;
     __shared__ int split_slot[kWs3MaxBlocks];  // partial slots of a split item, in block order
@@ -2298,7 +2298,10 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             tc::mbar_init(&b2_free[i], 1);
             tc::mbar_init(&drain[i], 1);
         }
-        for (int i = 0; i < kWs3MaxTileBufs; ++i) tc::mbar_init(&tile_full[i], 1);
+        for (int i = 0; i < kWs3MaxTileBufs; ++i) {
+            tc::mbar_init(&tile_full[i], 1);
+            tc::mbar_init(&tile_free[i], 1);
+        }
         tc::mbar_init(&d2_full, 1);
         tc::mbar_init(&d2_empty, 16);
         err_sh = 0;
@@ -2327,7 +2330,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
         // 4 control warps x 32 lanes x 32 registers + 16 epilogue warps x 32 lanes x 112 =
         // 61,440: exactly the 640 threads x 96 registers the block is launched with
         asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
-        uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_a = 0, ph_e2 = 0;
+        uint32_t ph_d1 = 0, ph_b2 = 0, ph_tile = 0, ph_free = 0, ph_a = 0, ph_e2 = 0;
         uint32_t pend = 0;  // copy thread: bulk copies in flight (bit j tile buffer j, bit 7 A1)
         uint32_t cph = 0;   // copy thread: parity of the phase the next copy into buffer j (bit j)
                             // or of A1 (bit 7) completes
@@ -2399,6 +2402,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                     issue_ss(K1 / 16, tmem + slot * a.d1_cols, tc::smem_u32(sA1), tc::smem_u32(buf(b)), 128 * 128,
                              N1 * 128, id1);
                     tc::mma_commit(&d1_full[slot]);
+                    tc::mma_commit(&tile_free[b]);  // the copy thread's signal that buffer b was read
                 };
                 bool good = wait_bit(&bar_a, ph_a, 0);
                 for (int j = 0; j < 2 && j < NU && good; ++j) {
@@ -2442,7 +2446,11 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 bool good = true;
                 int bu = 0, hu = 0, tu = 0;  // buffer, row part and frame of u
                 for (int u = 0; u < NU && good; ++u) {
-                    good = wait_bit(&d1_full[u & 1], ph_d1, u & 1);  // S1(u) done: buffer bu is free
+                    // S1(u) done: buffer bu is free.  Its own barrier, not d1_full[u & 1]: with
+                    // more than two buffers S1(u + 2) needs no refill from this thread, so
+                    // d1_full[u & 1] could complete twice before this wait and its parity alias;
+                    // tile_free[bu] cannot complete again before this thread refills bu
+                    good = wait_bit(&tile_free[bu], ph_free, bu);
                     if (good) pend &= ~((1u << bu) | 0x80u);  // its copy (and A1) had landed: S1(u) read them
                     if (good && u + NB < NU) copy_next(bu);
                     if (good && hu == 0 && tu + 1 + kTilePrefetch < nt)
