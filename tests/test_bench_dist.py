@@ -57,8 +57,10 @@ def test_recorded_traffic_only_for_the_captured_launch_configuration():
         assert got is None                         # kernel changed since the capture
         return
     assert got == pytest.approx(rec["bytes_per_sample"] * 250)
-    other = dict(rec["params"], chunk_mb=192)
+    other = dict(rec["params"], grid_frames=4)                 # another kernel variant: no record
     assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, other) is None
+    assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, dict(rec["params"], chunk_mb=24576)) == \
+        pytest.approx(rec["bytes_per_sample"] * 250)              # chunk size: not part of the key
     assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, cfg, None) is None
     import dataclasses
     assert bench.recorded_traffic("k_dftgemm_ws3", 3, 250, dataclasses.replace(cfg, input_bits=8),
