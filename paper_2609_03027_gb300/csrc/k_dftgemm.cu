@@ -2576,7 +2576,9 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
                 __syncwarp();
                 tc::fence_after_sync();
                 if (w)
-                    ws2_epilogue1<2>(tmem + lane_base + sl * a.d1_cols + p1 * nyh, nyh, yc0, yc1, imw, lane,
+                    // one TMEM load per round without row parts (fewer spills), two with them (a
+                    // short part's stores cannot hide a second round's load latency)
+                    ws2_epilogue1<PARTS ? 2 : 1>(tmem + lane_base + sl * a.d1_cols + p1 * nyh, nyh, yc0, yc1, imw, lane,
                                   sbase + a.sB2 + (size_t)sl * a.b2_bytes, 64 * P * hh + 64 * p1, R2);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
