@@ -148,3 +148,41 @@ def test_streaming_mix_station_types_match_oracle(path):
         print(f"{path} {cfg.name} T={cfg.n_time}: max error / peak {e.max():.2e}")
     for p in plans:
         p.close()
+
+
+@pytest.mark.gpu
+def test_small_and_large_blocks_under_concurrent_load_never_time_out():
+    # Stress for the tensor kernel's barrier hand-offs: thousands of short blocks (32 x 32
+    # grids, three or four tile buffers, many sub-frames per item) served four at a time next
+    # to long ones.  A copy thread that waited for buffer reuse on a barrier shared by two
+    # buffers once let one such block in about 3 000 run into its bounded wait; every block
+    # must complete with EPIC_OK and the small plan's images must equal its lone call's.
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    types = synth.mixed_station_types()
+    small = synth.serving_config(types[0], 128)              # 64-element station, 32 x 32 grid
+    large = synth.serving_config(types[1], 64)               # 256-element station, 128 x 128 grid
+    plans = [E.Plan.from_config(cfg, path="dftgemm", max_time=cfg.n_time) for cfg in (small, large)]
+    vs = [torch.from_numpy(synth.make_voltages(cfg)) for cfg in (small, large)]
+    ref = plans[0].image(vs[0].cuda())
+    torch.cuda.synchronize()
+    n_small = 8                                              # outputs of the small plan in flight
+    outs = [torch.empty_like(ref) for _ in range(n_small)]
+    out_large = torch.empty((large.n_chan, large.n_prod, large.grid_n, large.grid_n), device="cuda")
+    h = [v.pin_memory() for v in vs]
+    torch.cuda.synchronize()
+    with E.Server(device_bytes=4 * max(v.numel() for v in vs) + (64 << 20), slots=4) as srv:
+        tickets = []
+        for i in range(3000):
+            k, out = (1, out_large) if i % 10 == 9 else (0, outs[i % n_small])
+            t = None
+            while t is None:
+                t = srv.submit_ptr(plans[k], h[k].data_ptr(), (small, large)[k].n_time, out)
+            tickets.append(t)
+        for t in tickets:
+            srv.wait(t, timeout_ms=600000)                   # raises on any status but EPIC_OK
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    for p in plans:
+        p.close()
