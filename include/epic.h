@@ -186,6 +186,11 @@ epic_status epic_image(epic_plan_t plan, const uint8_t* volt, int T, void* strea
  * plan's device staging buffer, images it, copies the images to out_host
  * (C*n_prod*N*N floats; with EPIC_ACCUMULATE its old content is uploaded first)
  * and synchronises the stream before returning.  Pinned host memory is fastest.
+ * On the tensor path with several channel groups (and no sub-integrations or
+ * EPIC_ACCUMULATE) the copies overlap the computation: each group's voltages (its
+ * channel range of every sample) go up on a copy stream the plan owns, the group's
+ * kernels wait only for them, and its images come back while the next group
+ * computes; the images are the same.  EPIC_GRAPH is then ignored.
  * Returns EPIC_ERR_TIMEOUT when a bounded device-side wait ran out during this call
  * (or during an earlier call of the plan not yet reported by epic_sync). */
 epic_status epic_image_host(epic_plan_t plan, const uint8_t* volt_host, int T, void* stream,

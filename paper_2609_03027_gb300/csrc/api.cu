@@ -59,6 +59,8 @@ void free_plan(epic_plan_s* p)
         cudaEventDestroy(ev.stop);
     }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (cudaEvent_t ev : p->copy_ev) cudaEventDestroy(ev);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaSetDevice(cur);
     delete p;
 }
@@ -434,7 +436,8 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info)
 }  // extern "C"
 
 namespace epic {
-epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags)
+epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags,
+                      const GroupHooks* hooks)
 {
     const bool acc = (flags & EPIC_ACCUMULATE) != 0;
     p->timing = (flags & EPIC_TIME_KERNELS) != 0;
@@ -450,7 +453,7 @@ epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s
     switch (p->path) {
         case EPIC_PATH_PLAIN_FP32: return epic::plain_run(p, volt, T, s, out, acc);
         case EPIC_PATH_FUSED_FP32: return epic::fused_run(p, volt, T, s, out, acc);
-        case EPIC_PATH_DFTGEMM_FP16: return epic::dftgemm_run(p, volt, T, s, out, acc);
+        case EPIC_PATH_DFTGEMM_FP16: return epic::dftgemm_run(p, volt, T, s, out, acc, hooks);
     }
     return EPIC_ERR_INVALID_ARG;
 }
@@ -632,6 +635,60 @@ epic_status epic_image(epic_plan_t p, const uint8_t* volt, int T, void* stream, 
     return image_impl(p, volt, T, (cudaStream_t)stream, out, flags);
 }
 
+// epic_image_host for a tensor-path plan of several channel groups: group g's voltages (its
+// channel range of every sample, one 2-D copy) go to the device on the plan's copy stream,
+// its kernels wait only for them, and its images come back on the copy stream while the next
+// group computes; the call's stream waits for the copy stream at the end.  The staging
+// buffers were allocated by the caller; the previous call on the plan is complete.
+static epic_status image_host_pipelined(epic_plan_t p, const uint8_t* volt_host, int T, cudaStream_t s,
+                                        float* out_host, unsigned flags)
+{
+    const int groups = (p->C + p->tc.cg - 1) / p->tc.cg;
+    cudaError_t e = cudaSuccess;
+    if (!p->copy_stream) e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    while (e == cudaSuccess && p->copy_ev.size() < 2 * (size_t)groups + 1) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) p->copy_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "copy stream / events (host call)");
+    cudaStream_t cs = p->copy_stream;
+    const size_t fb = (size_t)p->A * p->P * (p->bits / 4);                   // one channel's frame
+    const size_t row = (size_t)p->C * fb;                                     // one time sample
+    const size_t ib = sizeof(float) * (size_t)p->nprod * p->N * p->N;         // one channel's images
+    int g = 0;
+    for (int c0 = 0; c0 < p->C && e == cudaSuccess; c0 += p->tc.cg, ++g) {  // every group's voltages
+        const int ng = std::min(p->tc.cg, p->C - c0);
+        e = cudaMemcpy2DAsync(p->stage_volt + c0 * fb, row, volt_host + c0 * fb, row, ng * fb, T,
+                              cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(p->copy_ev[2 * g], cs);
+    }
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaMemcpy2DAsync(H2D, host call)");
+    int gb = 0, ga = 0;
+    epic::GroupHooks hooks;
+    hooks.before = [&](int, int) {
+        const cudaError_t we = cudaStreamWaitEvent(s, p->copy_ev[2 * gb++], 0);
+        return we == cudaSuccess ? EPIC_OK : epic::cuda_fail(p, we, "cudaStreamWaitEvent(host call)");
+    };
+    hooks.after = [&](int c0, int ng) {
+        cudaEvent_t done = p->copy_ev[2 * ga++ + 1];
+        cudaError_t ae = cudaEventRecord(done, s);
+        if (ae == cudaSuccess) ae = cudaStreamWaitEvent(cs, done, 0);
+        if (ae == cudaSuccess)
+            ae = cudaMemcpyAsync(reinterpret_cast<uint8_t*>(out_host) + c0 * ib,
+                                 reinterpret_cast<uint8_t*>(p->stage_out) + c0 * ib, ng * ib,
+                                 cudaMemcpyDeviceToHost, cs);
+        return ae == cudaSuccess ? EPIC_OK : epic::cuda_fail(p, ae, "cudaMemcpyAsync(D2H, host call)");
+    };
+    epic_status st = epic::image_run(p, p->stage_volt, T, s, p->stage_out, flags & ~EPIC_GRAPH, &hooks);
+    e = cudaEventRecord(p->copy_ev[2 * groups], cs);  // the call's stream ends after the copies
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->copy_ev[2 * groups], 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st != EPIC_OK) return st;
+    if (e != cudaSuccess) return epic::cuda_fail(p, e, "cudaStreamSynchronize");
+    return take_timeout(p);
+}
+
 epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void* stream, float* out_host,
                             unsigned flags)
 {
@@ -660,6 +717,8 @@ epic_status epic_image_host(epic_plan_t p, const uint8_t* volt_host, int T, void
         }
         p->stage_bytes = vb + ob_max;
     }
+    if (p->path == EPIC_PATH_DFTGEMM_FP16 && p->sub == 0 && !(flags & EPIC_ACCUMULATE) && T > 0 && p->tc.cg < p->C)
+        return image_host_pipelined(p, volt_host, T, s, out_host, flags);
     const size_t tb = (size_t)T * p->C * p->A * p->P * (p->bits / 4);
     cudaError_t e = cudaSuccess;
     if (tb) e = cudaMemcpyAsync(p->stage_volt, volt_host, tb, cudaMemcpyHostToDevice, s);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,8 @@ struct epic_plan_s {
     size_t scratch_bytes = 0;
     int time_chunk = 0;
     uint8_t* stage_volt = nullptr;        // host-API staging
+    cudaStream_t copy_stream = nullptr;   // host-API copies overlapped with the tensor path's groups
+    std::vector<cudaEvent_t> copy_ev;
     float* stage_out = nullptr;
     size_t stage_bytes = 0;
     int sm_count = 0;
@@ -195,7 +198,15 @@ epic_status cuda_fail(epic_plan_s* p, cudaError_t e, const char* what);
 // new one; on failure the plan is back on its previous path and the status is returned).
 epic_status set_path(epic_plan_s* p, int path);
 // one epic_image call after argument checks (flags without EPIC_GRAPH handling)
-epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags);
+// Host-side hooks around each channel group of a tensor-path call: before(c0, ng) runs
+// before the group's first launch is issued, after(c0, ng) after its last (the pipelined
+// host-buffer call puts its per-group copies there).  Other paths ignore them.
+struct GroupHooks {
+    std::function<epic_status(int, int)> before, after;
+};
+
+epic_status image_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, unsigned flags,
+                      const GroupHooks* hooks = nullptr);
 // Grow c (zeroed on allocation) to what a call of p needs; allocates, so not on a hot path.
 epic_status call_scratch_fit(epic_plan_s* p, CallScratch& c);
 void call_scratch_free(CallScratch& c);
@@ -216,7 +227,8 @@ epic_status fused_set_slab(epic_plan_s* p, int SW);
 
 // k_dftgemm.cu
 epic_status dftgemm_setup(epic_plan_s* p);
-epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate);
+epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate,
+                        const GroupHooks* hooks = nullptr);
 epic_status dftgemm_grid_config(epic_plan_s* p, int F);
 epic_status dftgemm_set_chunk(epic_plan_s* p, size_t budget);
 epic_status dftgemm_set_kernel(epic_plan_s* p, int variant);

@@ -3417,7 +3417,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
     return EPIC_OK;
 }
 
-epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate)
+epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t s, float* out, bool accumulate,
+                        const GroupHooks* hooks)
 {
     const int C = p->C, P = p->P, A = p->A;
     MmaArgs a{};
@@ -3454,6 +3455,10 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     const int F = p->tc.grid_frames;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
         const int ng = std::min(p->tc.cg, C - c0);
+        if (hooks && hooks->before) {
+            const epic_status hs = hooks->before(c0, ng);
+            if (hs != EPIC_OK) return hs;
+        }
         for (int t0 = 0; t0 < T; t0 += p->tc.tc) {
             const int nt = std::min(p->tc.tc, T - t0);
             const dim3 gg((nt + fpc - 1) / fpc, ng);
@@ -3609,6 +3614,10 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
             ev_end(p, s);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(p, e, "tensor path launch");
+        }
+        if (hooks && hooks->after) {
+            const epic_status hs = hooks->after(c0, ng);
+            if (hs != EPIC_OK) return hs;
         }
     }
     return EPIC_OK;

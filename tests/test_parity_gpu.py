@@ -344,3 +344,29 @@ def test_pair_list_gridding_is_the_default_where_the_balanced_kernel_does_not_fi
     cfg = synth.config(3).subset([383], n_time=4)   # the tallest SKA-Low channel
     with E.Plan.from_config(cfg, path="dftgemm", max_time=4) as plan:
         assert plan.get_param("grid_kernel") == 3
+
+
+@pytest.mark.gpu
+def test_host_call_of_several_channel_groups_overlaps_copies_and_matches():
+    # The SKA-Low station (384 channels: three channel groups on the tensor path) through the
+    # host-buffer call, whose per-group copies run beside the other groups' kernels: the same
+    # images as the device call, bit for bit, in reset mode, in accumulate mode (one copy, no
+    # overlap) and for a pinned buffer given by pointer; and a channel of it against the oracle.
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    cfg = dataclasses.replace(synth.config(3), n_time=24)
+    v = synth.make_voltages(cfg)
+    with E.Plan.from_config(cfg, path="dftgemm", max_time=cfg.n_time) as plan:
+        dev = plan.image(torch.from_numpy(v).cuda()).cpu().numpy()
+        torch.cuda.synchronize()
+        host = plan.image_host(v)
+        assert np.array_equal(host, dev)
+        acc = plan.image_host(v, out=host.copy(), accumulate=True)
+        assert np.allclose(acc, 2 * dev, rtol=1e-6, atol=0)
+        hv = torch.from_numpy(v).pin_memory()
+        ho = torch.empty(dev.shape, dtype=torch.float32).pin_memory()
+        plan.image_host_ptr(hv.data_ptr(), cfg.n_time, ho.data_ptr(), graph=True)
+        assert np.array_equal(ho.numpy(), dev)
+    for c in (0, 200, 383):
+        ref = oracle_image(cfg, v, chans=[c])
+        assert_parity(host[c:c + 1], ref, "dftgemm", f"host call, channel {c}")
