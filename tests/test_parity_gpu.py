@@ -370,3 +370,37 @@ def test_host_call_of_several_channel_groups_overlaps_copies_and_matches():
     for c in (0, 200, 383):
         ref = oracle_image(cfg, v, chans=[c])
         assert_parity(host[c:c + 1], ref, "dftgemm", f"host call, channel {c}")
+
+
+@pytest.mark.parametrize("N", [8, 32, 128, 512])
+def test_plain_fft_forms_match_the_oracle(N):
+    # both FFT forms of the plain path (register-resident two-pass, shared-memory Stockham)
+    cfg = synth.small_config(n_ant=min(40, N * N // 8), n_chan=2, n_pol=2, grid_n=N, gcf_k=3, n_time=5,
+                             seed=70 + N, diameter_m=0.28 * N, sigma=0.7)
+    v = synth.make_voltages(cfg)
+    ref = oracle_image(cfg, v)
+    with E.Plan.from_config(cfg, path="plain") as plan:
+        d = torch.from_numpy(v).cuda()
+        assert plan.get_param("fft") == 0
+        a = plan.image(d).cpu().numpy()
+        plan.set_param("fft", 1)
+        b = plan.image(d).cpu().numpy()
+    assert_parity(a, ref, "plain", f"register FFT, N={N}")
+    assert_parity(b, ref, "plain", f"Stockham FFT, N={N}")
+
+
+def test_one_launch_for_every_channel_matches_channel_groups():
+    # group = 1: all 384 channels of the SKA-Low station in one launch per kernel (equal-cost
+    # shares) against the default channel groups; both against the oracle on sampled channels
+    cfg = dataclasses.replace(synth.config(3), n_time=16)
+    v = synth.make_voltages(cfg)
+    with E.Plan.from_config(cfg, path="dftgemm", max_time=cfg.n_time) as plan:
+        d = torch.from_numpy(v).cuda()
+        a = plan.image(d).cpu().numpy()
+        plan.set_param("group", 1)
+        assert plan.get_param("group") == 1
+        b = plan.image(d).cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(a).max())
+    for c in (0, 150, 300, 383):
+        ref = oracle_image(cfg, v, chans=[c])
+        assert_parity(b[c:c + 1], ref, "dftgemm", f"one launch, channel {c}")
