@@ -20,7 +20,8 @@
 // stay in registers over every frame of a chunk.
 //
 // Two kernels per (channel group, time chunk), stream-ordered; the grid tiles of a
-// chunk go through HBM between them (up to 3 GB per chunk, far more than L2):
+// chunk go through HBM between them (gigabytes per chunk, far more than L2; the
+// autotuner's chunk budget reaches 24 GiB, a whole block per channel group):
 //   k_dftgemm_grid_*  gather-grid every (t, c) frame of the chunk into FP16 tiles
 //                     already in the 128-byte swizzled UMMA K-major layout (tall
 //                     boxes: one such operand per row part)
