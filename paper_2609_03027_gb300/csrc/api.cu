@@ -85,6 +85,7 @@ void free_path_state(epic_plan_s* p)
     cudaFree(p->tc.gell_off);
     cudaFree(p->tc.tbox);
     cudaFree(p->tc.wcum);
+    cudaFree(p->tc.item_order);
     cudaFree(p->tc.pl_ptr);
     cudaFree(p->tc.pl_off);
     cudaFree(p->tc.pl_e);

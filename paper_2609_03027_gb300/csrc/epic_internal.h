@@ -57,6 +57,7 @@ struct TcState {
     int grid_max_list = 0;         // (cell, element) entries per channel
     int grid_variant = 1;          // 1: persistent row-major gather, 2: balanced task lists, 3: pair lists
     long long* wcum = nullptr;     // [C + 1] prefix sums of k_dftgemm_ws3 item costs per frame (work split)
+    int* item_order = nullptr;     // k_dftgemm_ws3 whole items: per channel group, the order items are dealt to blocks
     int* pl_ptr = nullptr;         // pair-list gridding: per channel entry offsets of the box's cell
     int* pl_off = nullptr;         //   pairs (row-major) and where each channel's start
     int* pl_e = nullptr;           //   entries: element

@@ -137,6 +137,7 @@ struct MmaArgs {
     const int4* tbox;           // k_dftgemm_ws3: per channel row parts (nyh, H, H nyh, 0)
     int nbt;                    // k_dftgemm_ws3: tile-part buffers in shared memory (2..4)
     const long long* wcum;      // k_dftgemm_ws3<1>: [C + 1] prefix sums of the channels' item costs per frame
+    const int* item_order;      // k_dftgemm_ws3<0>: per channel group (from c0 ipc), items in the order dealt to blocks
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b)
@@ -2351,6 +2352,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             } else {
                 item = blockIdx.x + it * gridDim.x;
                 if (item >= items) break;
+                if (a.item_order) item = a.item_order[(size_t)a.c0 * ipc + item];
                 fs = 0;
                 nt = a.nt;
             }
@@ -2496,6 +2498,7 @@ __global__ void __launch_bounds__(kWs3Threads, 1) k_dftgemm_ws3(MmaArgs a)
             } else {
                 item = blockIdx.x + it * gridDim.x;
                 if (item >= items) break;
+                if (a.item_order) item = a.item_order[(size_t)a.c0 * ipc + item];
                 fs = 0;
                 nt = a.nt;
             }
@@ -2672,6 +2675,8 @@ epic_status dftgemm_set_kernel(epic_plan_s* p, int variant)
     return EPIC_OK;
 }
 
+static epic_status upload_item_order(epic_plan_s* p);
+
 // Channels per launch of the warp-specialised kernels: 0 = groups of about two work items
 // per SM (whole items per block balance), 1 = every channel in one group (the fewest
 // launches; with equal (item, frame) shares the item count need not divide evenly).  The
@@ -2688,7 +2693,8 @@ epic_status dftgemm_set_group(epic_plan_s* p, int v)
         p->tc.cg = cg_old;
         dftgemm_set_chunk(p, p->chunk_budget);
     }
-    return st;
+    const epic_status so = upload_item_order(p);  // the groups changed
+    return st != EPIC_OK ? st : so;
 }
 
 // Work split of k_dftgemm_ws3: -1 = automatic (equal shares unless the launch's items are
@@ -2697,6 +2703,41 @@ epic_status dftgemm_set_split(epic_plan_s* p, int mode)
 {
     if (!p->tc.ws || mode < -1 || mode > 1 || (p->sub > 0 && mode == 1)) return EPIC_ERR_UNSUPPORTED;
     p->tc.split = mode;
+    return EPIC_OK;
+}
+
+// Order in which k_dftgemm_ws3 deals a channel group's whole work items to its blocks (block b
+// takes the items at positions b, b + G, b + 2 G, ... of the group's list, G blocks): items
+// sorted by modelled cost per frame (the work-split weight of their channel) and dealt in
+// snake order -- round k forward when k is even, backward when odd -- so that a block's
+// items add up to about the same cost (costliest with cheapest); a last partial round is
+// dealt forward, to the first blocks, as the kernel expects.
+static epic_status upload_item_order(epic_plan_s* p)
+{
+    cudaFree(p->tc.item_order);
+    p->tc.item_order = nullptr;
+    if (!p->tc.ws) return EPIC_OK;
+    const int C = p->C, ipc = p->tc.n_kb * p->tc.n_gp;
+    std::vector<int> ord((size_t)C * ipc);
+    for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
+        const int ng = std::min(p->tc.cg, C - c0), L = ng * ipc, G = std::min(L, p->sm_count);
+        auto w = [&](int i) {
+            const int4 r = p->tc.tbox_h[c0 + i / ipc];
+            return 1000LL + 1200LL * r.y + 10LL * r.z;
+        };
+        std::vector<int> idx(L);
+        for (int i = 0; i < L; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int u, int v) { return w(u) > w(v); });
+        for (int r = 0; r < L; ++r) {
+            const int k = r / G, j = r % G;
+            const bool partial = (k + 1) * G > L;
+            const int b = (k & 1) && !partial ? G - 1 - j : j;
+            ord[(size_t)c0 * ipc + (size_t)k * G + b] = idx[r];
+        }
+    }
+    cudaError_t e = cudaMalloc(&p->tc.item_order, ord.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(p->tc.item_order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(p, e, "work-item order upload");
     return EPIC_OK;
 }
 
@@ -3127,6 +3168,8 @@ epic_status dftgemm_setup(epic_plan_s* p)
     p->tc.stride = stride;
     epic_status cst = dftgemm_set_chunk(p, kScratchBudget);
     if (cst != EPIC_OK) return cst;
+    cst = upload_item_order(p);
+    if (cst != EPIC_OK) return cst;
 
     // gridding kernel: the persistent one when the cell lists of the largest channel fit in
     // shared memory next to F frames of voltages, else the gather kernel reading them through L1
@@ -3452,6 +3495,7 @@ epic_status dftgemm_run(epic_plan_s* p, const uint8_t* volt, int T, cudaStream_t
     a.tbox = p->tc.tbox;
     a.nbt = p->tc.nbt;
     a.wcum = p->tc.wcum;
+    a.item_order = p->tc.item_order;
     const int fpc = kGridFramesPerBlock;
     const int F = p->tc.grid_frames;
     for (int c0 = 0; c0 < C; c0 += p->tc.cg) {
