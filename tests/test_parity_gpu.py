@@ -367,6 +367,12 @@ def test_host_call_of_several_channel_groups_overlaps_copies_and_matches():
         ho = torch.empty(dev.shape, dtype=torch.float32).pin_memory()
         plan.image_host_ptr(hv.data_ptr(), cfg.n_time, ho.data_ptr(), graph=True)
         assert np.array_equal(ho.numpy(), dev)
+        plan.set_param("chunk_mb", 96)                   # several time chunks inside each group
+        assert plan.info()["time_chunk"] < cfg.n_time
+        dev2 = plan.image(torch.from_numpy(v).cuda()).cpu().numpy()
+        torch.cuda.synchronize()
+        assert np.array_equal(plan.image_host(v), dev2)
+        assert np.allclose(dev2, dev, rtol=1e-5, atol=1e-6 * np.abs(dev).max())
     for c in (0, 200, 383):
         ref = oracle_image(cfg, v, chans=[c])
         assert_parity(host[c:c + 1], ref, "dftgemm", f"host call, channel {c}")
